@@ -1,0 +1,92 @@
+"""Multi-material frame: tile classification, binning and per-pixel decode.
+
+Paper Sec. 4 ("Tile-based classification") and Algorithm 1: the screen is cut
+into tiles; pass A marks each tile as having no neural pixel, one network for
+all its valid pixels and more than half of them valid ("uniform"), or anything
+else ("mixed"); pass B gives every valid pixel of a mixed tile a slot in a
+per-network packed list, so that networks run on tiles whose pixels share one
+MLP.  The slot offsets per network are an exclusive prefix sum of the
+per-network counts (Algorithm 1 reads them but does not say how they are
+made).  Here a tile is 128 pixels (tile_w x tile_h) and each network's packed
+list starts on a multiple of 128 slots, so every packed tile holds one network.
+
+The per-pixel decode follows Sec. 3.1 with the texture unit's mip-mapped
+filter of Sec. 3.2 / Sec. 3.3: per latent level k, lod_k = lod + log2(W_k)
+(lod = log2 of the uv footprint of one pixel, plus the mip bias), clamped to
+the level's mip range, trilinear with wrap addressing; the MLP runs in the
+FP16 form (see `emulate`).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import bc1, emulate
+from .sample import trilinear
+
+EMPTY, UNIFORM, MIXED = 0, 1, 2
+
+
+def classify(mat_id: np.ndarray, tile_w: int, tile_h: int):
+    """Per tile (row-major over tiles): (kind, material of a uniform tile or -1)."""
+    h, w = mat_id.shape
+    assert h % tile_h == 0 and w % tile_w == 0
+    t = mat_id.reshape(h // tile_h, tile_h, w // tile_w, tile_w).transpose(0, 2, 1, 3)
+    t = t.reshape(-1, tile_w * tile_h).astype(np.int64)
+    valid = t >= 0
+    count = valid.sum(axis=1)
+    big = np.iinfo(np.int64).max
+    mn = np.where(valid, t, big).min(axis=1)
+    mx = np.where(valid, t, -1).max(axis=1)
+    kind = np.where(count == 0, EMPTY, np.where((mn == mx) & (count * 2 > tile_w * tile_h), UNIFORM, MIXED))
+    mat = np.where(kind == UNIFORM, mn, -1)
+    return kind, mat
+
+
+def tile_pixels(tile: int, w: int, tile_w: int, tile_h: int) -> np.ndarray:
+    """Linear pixel indices of a tile, row-major inside the tile."""
+    tiles_x = w // tile_w
+    ty, tx = divmod(tile, tiles_x)
+    yy, xx = np.meshgrid(np.arange(tile_h), np.arange(tile_w), indexing="ij")
+    return ((ty * tile_h + yy) * w + tx * tile_w + xx).reshape(-1)
+
+
+def mixed_counts(mat_id: np.ndarray, kind: np.ndarray, tile_w: int, tile_h: int, m: int):
+    """Per-material count of valid pixels lying in mixed tiles, and the exclusive
+    scan of those counts rounded up to whole 128-slot tiles (slot offsets)."""
+    h, w = mat_id.shape
+    flat = mat_id.reshape(-1)
+    counts = np.zeros(m, dtype=np.int64)
+    for tile in np.nonzero(kind == MIXED)[0]:
+        ids = flat[tile_pixels(tile, w, tile_w, tile_h)]
+        ids = ids[ids >= 0]
+        counts += np.bincount(ids, minlength=m)
+    per = tile_w * tile_h
+    padded = (counts + per - 1) // per * per
+    offsets = np.concatenate([[0], np.cumsum(padded)[:-1]])
+    return counts, offsets
+
+
+def decode_pixels(material, levels_mips_rgb: list, uv: np.ndarray, lod: np.ndarray,
+                  precision: str = "fp16") -> np.ndarray:
+    """Decode the given pixels of one material: uv [n, 2], lod [n] -> [n, N]."""
+    u, v = uv[:, 0].astype(np.float64), uv[:, 1].astype(np.float64)
+    feats = []
+    for lv, mips in zip(material.levels, levels_mips_rgb):
+        lam = lod.astype(np.float64) + np.log2(float(lv.width))
+        feats.append(trilinear(mips, u, v, lam, lv.shift, material.address))
+    x = np.concatenate(feats, axis=-1)
+    mlp = material.mlp
+    if precision == "fp16":
+        return emulate.forward_fp16(x, mlp.weights, mlp.biases)
+    from . import mlp as mlp_mod
+    return mlp_mod.forward(x, mlp.weights, mlp.biases)
+
+
+def level_mips_rgb(level) -> list:
+    """Decoded mips of a BC1 latent level as FP64 [h, w, 3] in [0, 1]."""
+    out = []
+    w, h = level.width, level.height
+    for blocks in level.blocks:
+        out.append(bc1.decode_level(blocks, w, h).astype(np.float64) / 255.0)
+        w, h = max(4, w // 2), max(4, h // 2)
+    return out
