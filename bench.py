@@ -1,0 +1,310 @@
+"""Benchmark of the neural block texture decode on GB300.
+
+One step = one fused decode (BC1 fetch + decode, bilinear sampling of 4 latent
+levels, MLP) of a whole 4096^2 9-channel texture set: the 1024^2..128^2 BC1
+pyramid, MLP 12-64-64-9, FP32 SIMT form, texel-centre grid, FP32 output.
+`value` is output texels per second over all ranks (weak scaling: every rank
+decodes its own texture set).  Extra forms (the FP16 / FP8 tensor-core decode
+of the 12-64-64-64-9 set, the training step, the batched multi-material
+decode) are timed in the same run and reported under "forms".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle (the only reference this method has:
+the paper ships no code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Gtexel/s fused BC1+MLP decode, FP16-TC vs FP32, at stated error; train step/s"
+WORKLOAD = "decode-4096sq-bc1x4-mlp12-64-64-9-fp32"
+FLOP_PER_TEXEL_C1 = 2 * (12 * 64 + 64 * 64 + 64 * 9)  # 10,880
+SM_COUNT_GB300, FP32_LANES_PER_SM = 152, 128
+
+
+def _peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+            "source": "fallback"}
+
+
+def _fp32_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FFMA peak: SMs x 128 FP32 lanes x 2 FLOP x clock."""
+    return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- CPU oracle leg
+
+def _oracle_sample(n_texels: int, seed: int = 11) -> dict:
+    """Times the FP64 oracle on n_texels random texels of the 4096^2 workload
+    (BC1 level decode included).  Runs in a fresh process with one BLAS thread."""
+    import oracle
+    wl = synth.decode_workload(1)
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, 4096 * 4096, n_texels)
+    t0 = time.perf_counter()
+    tex = [oracle.decode.level_rgb(lv) for lv in wl.material.levels]
+    for c in range(0, n_texels, 1 << 16):
+        oracle.decode.decode_grid(wl.material, 4096, 4096, idx[c:c + (1 << 16)], tex=tex)
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "texels": n_texels}
+
+
+def cpu_baseline(n_texels: int = 1 << 22) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._oracle_sample(%d)))" % (ROOT, n_texels))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    gts = r["texels"] / r["seconds"] / 1e9
+    return {"value": gts, "unit": "Gtexel/s", "cores": 1, "kind": "oracle",
+            "sample": f"{r['texels']} random texels of the 4096^2 decode (FP64 numpy oracle, BC1 level decode "
+                      f"included, one BLAS thread), {r['seconds']:.1f} s"}
+
+
+# ---------------------------------------------------------------------------- GPU legs
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args) -> dict | None:
+    import torch
+
+    import paper_2506_06040_gb300 as nb
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+    ctx = nb.Context(local)
+    stream = torch.cuda.current_stream()
+
+    wl = synth.decode_workload(1)
+    mat = nb.Material.from_synth(wl.material)
+    W = H = args.side
+    n = W * H
+    out = torch.empty((n, 9), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 256 MB > 129 MB L2
+
+    def step():
+        nb.decode(ctx, mat, grid=(W, H), out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    # timed region: per-step events around the decode only, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    gpu_id = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else str(gpu_id or local)
+    clocks = ClockSampler(gpu_id)
+    _barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 255)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    _barrier(world)
+    clk = clocks.stop()
+    ctx.sync()
+    times = [a.elapsed_time(b) for a, b in ev]  # ms
+    ms_step = _max_over_ranks(sum(times) / len(times), world)
+    kernel_ms = statistics.mean(times)
+    value = world * n / (ms_step * 1e-3) / 1e9
+
+    # e2e through the public API with host buffers: inputs H2D from pinned memory,
+    # decode, decoded texture D2H to pinned memory, every step
+    host_blocks = [torch.from_numpy(lv.packed().view(np.int64)).pin_memory() for lv in wl.material.levels]
+    host_w, host_b = mat.weights.cpu().pin_memory(), mat.biases.cpu().pin_memory()
+    host_out = torch.empty((n, 9), dtype=torch.float32).pin_memory()
+    h2d = sum(b.numel() * 8 for b in host_blocks) + host_w.numel() * 4 + host_b.numel() * 4
+    d2h = host_out.numel() * 4
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_steps = max(2, min(args.steps, 5))
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e_steps):
+        for d, h in zip(mat.blocks, host_blocks):
+            d.copy_(h, non_blocking=True)
+        mat.weights.copy_(host_w, non_blocking=True)
+        mat.biases.copy_(host_b, non_blocking=True)
+        step()
+        host_out.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = _max_over_ranks(e0.elapsed_time(e1) / e_steps, world)
+    e2e = world * n / (e2e_ms * 1e-3) / 1e9
+
+    flop = FLOP_PER_TEXEL_C1 * n
+    peak_tf = _fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    achieved_tf = flop / (kernel_ms * 1e-3) / 1e12
+    res = {
+        "metric": METRIC, "value": value, "unit": "Gtexel/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "texels_per_step": n, "out_bytes_per_step": n * 36,
+                   "latent_levels": [1024, 512, 256, 128], "mlp": [12, 64, 64, 9], "parallelism": f"replicas{world}",
+                   "l2": "256 MB buffer written between timed steps; the 604 MB output also exceeds L2"},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / peak_tf, "traffic": None,
+                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
+                     "kernel": "k_decode_fp32<64,2,9,2>", "kernel_ms": kernel_ms},
+        "e2e": {"value": e2e, "unit": "Gtexel/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return res if rank == 0 else None
+
+
+def run_reference(args) -> dict | None:
+    rank, world, _ = _dist()
+    if rank != 0:
+        return None
+    per_step = 1 << 17
+    for _ in range(args.warmup):
+        _oracle_sample(1 << 14)
+    t0 = time.perf_counter()
+    texels = 0
+    for i in range(args.steps):
+        r = _oracle_sample(per_step, seed=100 + i)
+        texels += r["texels"]
+    dt = time.perf_counter() - t0
+    v = texels / dt / 1e9
+    return {"metric": METRIC, "value": v, "unit": "Gtexel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": "Gtexel/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{per_step} random texels per step of the 4096^2 decode (FP64 numpy oracle)"},
+            "e2e": {"value": v, "unit": "Gtexel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=4096, help="output side (4096 = the benchmark workload; "
+                    "smaller sides are for profiling captures)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        rank, world, _ = _dist()
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline()  # before the first GPU call (fresh process, spawn-safe)
+        res = run_ours(args)
+        if res is not None:
+            res["cpu_baseline"] = cpu
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * nbtc.h -- C ABI of the GB300 neural block texture decoder.
+ *
+ * The method ("Hardware Accelerated Neural Block Texture Compression with
+ * Cooperative Vectors", arXiv 2506.06040) stores a material as L latent
+ * textures in BC1 format (Sec. 3.1, "Latent BC1 compression") and decodes the
+ * texel at uv by sampling each latent level, concatenating the features and
+ * running a small ReLU MLP that outputs the material channels (Sec. 3.1,
+ * "Network Architecture").  This library runs that decode, its training step
+ * on continuous latents (Sec. 3.2) and the multi-material tile pipeline of
+ * Sec. 4 as CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named *_dev, and every pointer inside the descriptor structs,
+ *    are device pointers.  All buffers belong to the caller; the library never
+ *    frees them and keeps no reference after the call's work has run.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Every call is asynchronous and stream-ordered unless it says
+ *    otherwise.
+ *  - Synchronous argument checks return NBTC_ERR_INVALID_ARG or
+ *    NBTC_ERR_UNSUPPORTED before anything is enqueued; a failed launch returns
+ *    NBTC_ERR_CUDA.  Faults the kernels detect themselves (a bounded wait that
+ *    ran out, an index outside its buffer in a checked build) are written to
+ *    the context's device status word and reported by nbtc_status_sync().
+ *    nbtc_last_error() gives a human-readable message for the calling thread.
+ *  - Texel (x, y) of a W x H image is element y * W + x (row-major); u runs
+ *    along x, v along y, origin at the top-left corner, texel centres at
+ *    half-integers (texel coordinate x = u * W - 0.5 + shift).
+ *  - Outputs are texel-major: N contiguous channels per texel.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef NBTC_H
+#define NBTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NBTC_MAX_LEVELS 8
+#define NBTC_MAX_LAYERS 4
+#define NBTC_MAX_MIPS 16
+
+typedef enum {
+  NBTC_OK = 0,
+  NBTC_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or descriptor   */
+  NBTC_ERR_UNSUPPORTED = 2, /* valid request this build has no kernel for    */
+  NBTC_ERR_CUDA = 3,        /* a CUDA runtime call failed                    */
+  NBTC_ERR_TIMEOUT = 4,     /* a device-side bounded wait expired            */
+  NBTC_ERR_BOUNDS = 5       /* a checked build caught an out-of-range index  */
+} nbtc_status;
+
+typedef enum {
+  NBTC_FP32 = 0,     /* FP32 SIMT arithmetic (FFMA), FP32 output              */
+  NBTC_FP16 = 1,     /* FP16 operands on tcgen05, FP32 accumulate, FP16 output */
+  NBTC_FP8_E4M3 = 2  /* E4M3 operands on tcgen05 with per-layer power-of-two
+                        scales, FP32 accumulate, FP16 output                   */
+} nbtc_precision;
+
+typedef enum { NBTC_CLAMP = 0, NBTC_WRAP = 1 } nbtc_address;
+
+typedef enum { NBTC_LOSS_MSE = 0, NBTC_LOSS_L1 = 1 } nbtc_loss;
+
+/* One BC1 latent texture T_k (Sec. 3.1).  `blocks` holds mip 0 then mips
+ * 1 .. num_mips-1 back to back; mip m is max(4, width>>m) x max(4, height>>m)
+ * texels, each mip a row-major array of 8-byte BC1 blocks (block (bx, by) at
+ * by * (w_m / 4) + bx).  Block bits 0-15 hold endpoint c0, 16-31 endpoint c1
+ * (RGB565), 32-63 the sixteen 2-bit indices, texel (tx, ty) at bit
+ * 2 * (4 ty + tx).  `shift` offsets the sample position by that many texels on
+ * both axes (the paper shifts the 2nd and 4th latent by half a texel). */
+typedef struct {
+  const uint64_t* blocks;
+  int32_t width;    /* mip-0 texels, multiple of 4, >= 4 */
+  int32_t height;   /* mip-0 texels, multiple of 4, >= 4 */
+  int32_t num_mips; /* 1 .. NBTC_MAX_MIPS */
+  float shift;
+} nbtc_level;
+
+/* The latent pyramid of one material: features are ordered
+ * [T_0.rgb, T_1.rgb, ...]; `address` is an nbtc_address. */
+typedef struct {
+  int32_t num_levels; /* 1 .. NBTC_MAX_LEVELS (the fast kernels: 4) */
+  int32_t address;
+  nbtc_level levels[NBTC_MAX_LEVELS];
+} nbtc_latents;
+
+/* ReLU MLP f(x) (Sec. 3.1): num_layers linear layers, ReLU after all but the
+ * last.  Layer l maps dims[l] -> dims[l+1]; its weight is row-major
+ * [dims[l+1]][dims[l]] (out x in) and the layers are stored back to back in
+ * `weights`; `biases` likewise.  FP32, device memory. */
+typedef struct {
+  int32_t num_layers; /* 2 .. NBTC_MAX_LAYERS */
+  int32_t dims[NBTC_MAX_LAYERS + 1];
+  const float* weights;
+  const float* biases;
+} nbtc_mlp;
+
+typedef struct nbtc_context nbtc_context;
+
+/* ------------------------------------------------------------------ context */
+
+/* Creates a context on CUDA device `device` (made current for the call).  The
+ * context owns a 4-byte device status word and nothing else per device.
+ * Returns NBTC_ERR_INVALID_ARG for a NULL `ctx`, NBTC_ERR_UNSUPPORTED when the
+ * device is not compute capability 10.3, NBTC_ERR_CUDA when CUDA fails. */
+nbtc_status nbtc_create(int device, nbtc_context** ctx);
+
+/* Frees the context (synchronises the device first).  NULL is accepted. */
+nbtc_status nbtc_destroy(nbtc_context* ctx);
+
+/* Waits for `stream`, then returns and clears the device status word: NBTC_OK
+ * or the first fault a kernel recorded since the last call (TIMEOUT, BOUNDS). */
+nbtc_status nbtc_status_sync(nbtc_context* ctx, void* stream);
+
+/* Static description of a status code. */
+const char* nbtc_status_string(nbtc_status s);
+
+/* Message describing the last non-OK return on the calling thread ("" if none). */
+const char* nbtc_last_error(void);
+
+/* Tests only: caps every device-side bounded wait of this context at
+ * `spins` iterations (0 restores the default budget). */
+nbtc_status nbtc_set_wait_budget(nbtc_context* ctx, int64_t spins);
+
+/* ------------------------------------------------------------------ decode */
+
+/* BC1 decode of one mip of one latent level to RGB8 (Sec. 3.1 with the BC1
+ * format definition the paper cites; integer, bit-exact): out_dev receives
+ * h_m x w_m x 3 bytes, row-major.  Rounding: channels expand to 8 bits by bit
+ * replication; when c0 > c1 (raw 16-bit compare) the palette is
+ * {c0, c1, (2 c0 + c1 + 1) / 3, (c0 + 2 c1 + 1) / 3}, otherwise
+ * {c0, c1, (c0 + c1 + 1) / 2, black}, integer division, per channel. */
+nbtc_status nbtc_bc1_decode_level(nbtc_context* ctx, const nbtc_level* level, int32_t mip,
+                                  uint8_t* out_dev, void* stream);
+
+/* Bytes nbtc_pack_mlp() writes for `mlp` in `precision` (0 for NBTC_FP32,
+ * which reads the FP32 weights directly). */
+nbtc_status nbtc_packed_mlp_bytes(const nbtc_mlp* mlp, int32_t precision, size_t* bytes);
+
+/* Lays the MLP out for the tensor-core forms: weights converted to FP16 or
+ * E4M3 (round to nearest even, E4M3 saturating) in the shared-memory image the
+ * decode kernel copies in one bulk transfer, plus FP32 biases and scales.
+ * For NBTC_FP8_E4M3 `act_absmax_dev` must hold, per layer, the largest
+ * magnitude of that layer's input over a calibration set (nbtc_fp8_calibrate);
+ * the layer scales are then sw_l = pow2ceil(absmax(W_l) / 448) and
+ * sa_l = pow2ceil(act_absmax_l / 448).  `packed_dev` must be 16-byte aligned
+ * and at least nbtc_packed_mlp_bytes() long. */
+nbtc_status nbtc_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int32_t precision,
+                          const float* act_absmax_dev, void* packed_dev, size_t packed_bytes,
+                          void* stream);
+
+/* FP8 calibration: runs the FP32 decode on the texel-centre sub-grid of every
+ * `step`-th texel in x and y of a grid_w x grid_h output and writes, per layer
+ * l, max |input of layer l| to act_absmax_dev[l] (num_layers floats). */
+nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp,
+                               int32_t grid_w, int32_t grid_h, int32_t step,
+                               float* act_absmax_dev, void* stream);
+
+/* Neural decode (Sec. 3.1): for each output texel, BC1 fetch + decode of
+ * every latent level, bilinear sample at uv (level shift, clamp or wrap),
+ * concatenation, MLP.
+ *  - uv_dev == NULL: grid mode, n == grid_w * grid_h texel-centre outputs,
+ *    u = (i + 0.5) / grid_w, v = (j + 0.5) / grid_h, row-major.
+ *  - uv_dev != NULL: n (u, v) FP32 pairs, interleaved; grid_w, grid_h ignored.
+ *  - precision NBTC_FP32: `packed_dev` NULL, `out_dev` n x N FP32.
+ *    NBTC_FP16 / NBTC_FP8_E4M3: `packed_dev` from nbtc_pack_mlp() with the
+ *    same precision, `out_dev` n x N FP16.  out_dev 16-byte aligned.
+ * Shapes with a kernel: 4 latent levels, hidden width 16, 32 or 64 (all
+ * hidden layers equal), 1-3 hidden layers, N <= 16 (tensor-core forms: hidden
+ * width 64, N <= 16). */
+nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp,
+                        int32_t precision, const void* packed_dev, const float* uv_dev,
+                        int64_t n, int32_t grid_w, int32_t grid_h, void* out_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBTC_H */

@@ -1,0 +1,10 @@
+"""GB300-native neural block texture decode (arXiv 2506.06040).
+
+Python face of the C-ABI library `libnbtc.so` (include/nbtc.h): PyTorch holds
+device memory and streams; every step of the decode, training and batching
+paths runs in the library's CUDA kernels.  Build the library with
+`paper_2506_06040_gb300.build.build()` (or `__graft_entry__.build()`).
+"""
+from ._abi import (CLAMP, FP8_E4M3, FP16, FP32, LOSS_L1, LOSS_MSE, WRAP, NbtcError,  # noqa: F401
+                   load)
+from .api import Context, Material, bc1_decode_level, decode, fp8_calibrate, pack_mlp  # noqa: F401

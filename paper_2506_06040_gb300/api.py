@@ -1,0 +1,156 @@
+"""Thin torch-facing wrappers over the C ABI (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_size_t, c_void_p
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check
+
+
+def _stream(stream) -> c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> c_void_p:
+    return c_void_p(0 if t is None else t.data_ptr())
+
+
+class Context:
+    """A library context on one CUDA device (owns the device status word)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _abi.load()
+        self.device = device
+        h = c_void_p()
+        check(self.lib.nbtc_create(device, byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self.lib.nbtc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        """Waits for the stream and raises if a kernel recorded a fault."""
+        check(self.lib.nbtc_status_sync(self.handle, _stream(stream)))
+
+    def status(self, stream=None) -> int:
+        return self.lib.nbtc_status_sync(self.handle, _stream(stream))
+
+    def set_wait_budget(self, spins: int):
+        check(self.lib.nbtc_set_wait_budget(self.handle, spins))
+
+
+class Material:
+    """Device copy of a material: BC1 latent levels (with mips) and an FP32 MLP.
+
+    levels: list of (blocks: uint64 array of all mips back to back, width, height,
+    num_mips, shift); weights[l]: [out, in] FP32; biases[l]: [out] FP32."""
+
+    def __init__(self, levels, weights, biases, address: int = _abi.CLAMP, device="cuda"):
+        self.device = torch.device(device)
+        self.blocks, self.level_meta = [], []
+        for blocks, w, h, mips, shift in levels:
+            b = np.ascontiguousarray(np.asarray(blocks, dtype=np.uint64)).view(np.int64)
+            self.blocks.append(torch.from_numpy(b).to(self.device))
+            self.level_meta.append((int(w), int(h), int(mips), float(shift)))
+        self.dims = [int(weights[0].shape[1])] + [int(w.shape[0]) for w in weights]
+        self.weights = torch.from_numpy(np.concatenate([np.asarray(w, np.float32).ravel() for w in weights])).to(self.device)
+        self.biases = torch.from_numpy(np.concatenate([np.asarray(b, np.float32).ravel() for b in biases])).to(self.device)
+        self.address = address
+
+    @classmethod
+    def from_synth(cls, mat, device="cuda"):
+        levels = [(lv.packed(), lv.width, lv.height, lv.num_mips, lv.shift) for lv in mat.levels]
+        addr = _abi.WRAP if mat.address == "wrap" else _abi.CLAMP
+        return cls(levels, mat.mlp.weights, mat.mlp.biases, addr, device)
+
+    @property
+    def n_out(self) -> int:
+        return self.dims[-1]
+
+    def latents_struct(self) -> _abi.Latents:
+        s = _abi.Latents()
+        s.num_levels = len(self.blocks)
+        s.address = self.address
+        for k, (b, (w, h, mips, shift)) in enumerate(zip(self.blocks, self.level_meta)):
+            s.levels[k] = _abi.Level(b.data_ptr(), w, h, mips, shift)
+        return s
+
+    def level_struct(self, k: int) -> _abi.Level:
+        w, h, mips, shift = self.level_meta[k]
+        return _abi.Level(self.blocks[k].data_ptr(), w, h, mips, shift)
+
+    def mlp_struct(self) -> _abi.Mlp:
+        s = _abi.Mlp()
+        s.num_layers = len(self.dims) - 1
+        for i, d in enumerate(self.dims):
+            s.dims[i] = d
+        s.weights = self.weights.data_ptr()
+        s.biases = self.biases.data_ptr()
+        return s
+
+
+def bc1_decode_level(ctx: Context, mat: Material, k: int, mip: int = 0, stream=None) -> torch.Tensor:
+    w, h, _, _ = mat.level_meta[k]
+    for _ in range(mip):
+        w, h = max(4, w // 2), max(4, h // 2)
+    out = torch.empty((h, w, 3), dtype=torch.uint8, device=mat.device)
+    lv = mat.level_struct(k)
+    check(ctx.lib.nbtc_bc1_decode_level(ctx.handle, byref(lv), mip, _ptr(out), _stream(stream)))
+    return out
+
+
+def packed_mlp_bytes(mat: Material, precision: int) -> int:
+    n = c_size_t()
+    m = mat.mlp_struct()
+    check(_abi.load().nbtc_packed_mlp_bytes(byref(m), precision, byref(n)))
+    return n.value
+
+
+def fp8_calibrate(ctx: Context, mat: Material, grid_w: int, grid_h: int, step: int = 16,
+                  stream=None) -> torch.Tensor:
+    absmax = torch.empty(len(mat.dims) - 1, dtype=torch.float32, device=mat.device)
+    lat, m = mat.latents_struct(), mat.mlp_struct()
+    check(ctx.lib.nbtc_fp8_calibrate(ctx.handle, byref(lat), byref(m), grid_w, grid_h, step,
+                                     _ptr(absmax), _stream(stream)))
+    return absmax
+
+
+def pack_mlp(ctx: Context, mat: Material, precision: int, act_absmax=None, stream=None) -> torch.Tensor:
+    nbytes = packed_mlp_bytes(mat, precision)
+    packed = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=mat.device)
+    m = mat.mlp_struct()
+    check(ctx.lib.nbtc_pack_mlp(ctx.handle, byref(m), precision, _ptr(act_absmax), _ptr(packed), nbytes,
+                                _stream(stream)))
+    return packed
+
+
+def decode(ctx: Context, mat: Material, precision: int = _abi.FP32, packed=None, uv=None, grid=None,
+           out=None, stream=None) -> torch.Tensor:
+    """Decodes n texels: grid=(w, h) texel centres, or uv [n, 2] FP32 on the device.
+    Returns [n, N] FP32 (FP32 form) or FP16 (tensor-core forms)."""
+    if uv is not None:
+        assert uv.dtype == torch.float32 and uv.is_contiguous() and uv.dim() == 2 and uv.shape[1] == 2
+        n, gw, gh = uv.shape[0], 0, 0
+    else:
+        gw, gh = grid
+        n = gw * gh
+    dt = torch.float32 if precision == _abi.FP32 else torch.float16
+    if out is None:
+        out = torch.empty((n, mat.n_out), dtype=dt, device=mat.device)
+    lat, m = mat.latents_struct(), mat.mlp_struct()
+    check(ctx.lib.nbtc_decode(ctx.handle, byref(lat), byref(m), precision, _ptr(packed), _ptr(uv), n, gw, gh,
+                              _ptr(out), _stream(stream)))
+    return out

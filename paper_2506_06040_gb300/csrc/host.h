@@ -1,0 +1,45 @@
+// Host-side internals shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "common.cuh"
+
+struct nbtc_context {
+  int device = 0;
+  int sm_count = 0;
+  int* status_dev = nullptr;       // device status word (first recorded fault)
+  long long wait_budget = 0;       // spins per bounded device wait (0 = default)
+};
+
+namespace nbtc {
+
+// Records `msg` as the calling thread's last error and returns `code`.
+nbtc_status fail(nbtc_status code, const std::string& msg);
+// Wraps a CUDA runtime result: NBTC_OK, or NBTC_ERR_CUDA with the CUDA message.
+nbtc_status cuda_check(cudaError_t err, const char* what);
+
+// Makes ctx->device current for the rest of the call.
+nbtc_status enter(nbtc_context* ctx);
+
+// Validates a latent pyramid for the decode kernels and fills the device
+// views of mip `mip` of each level.
+nbtc_status make_level_views(const nbtc_latents* lat, int mip, LevelView* views);
+
+// Validates an MLP descriptor (shape and pointers).
+nbtc_status check_mlp(const nbtc_mlp* mlp);
+
+constexpr long long kDefaultWaitBudget = 1ll << 26;
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Kernel launchers (one per translation unit).
+nbtc_status launch_bc1_decode(nbtc_context* ctx, const LevelView& v, uint8_t* out, cudaStream_t s);
+nbtc_status launch_decode_fp32(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp,
+                               cudaStream_t s);
+nbtc_status launch_calibrate_fp32(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp,
+                                  int step, float* absmax, cudaStream_t s);
+
+}  // namespace nbtc

@@ -1,0 +1,142 @@
+"""GPU parity of the BC1 decode (bit-exact) and the FP32 fused decode
+(max abs error 1e-5 against the FP64 oracle), through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import max_abs, require_gpu
+
+pytestmark = pytest.mark.gpu
+TOL_FP32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def nb():
+    require_gpu()
+    import paper_2506_06040_gb300 as nb
+    return nb
+
+
+@pytest.fixture(scope="module")
+def ctx(nb):
+    c = nb.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_bc1_every_texel_every_level(nb, ctx, k):
+    wl = synth.decode_workload(k)
+    mat = nb.Material.from_synth(wl.material)
+    for i, lv in enumerate(wl.material.levels):
+        got = nb.bc1_decode_level(ctx, mat, i).cpu().numpy()
+        want = oracle.bc1.decode_level(lv.blocks[0], lv.width, lv.height)
+        assert np.array_equal(got, want), f"level {i}"
+    ctx.sync()
+
+
+def test_bc1_mips_and_golden_blocks(nb, ctx):
+    bw = synth.batch_workload(num_materials=1, frame_w=32, frame_h=16, smin=512, smax=512)
+    m = bw.materials[0]
+    mat = nb.Material.from_synth(m)
+    for i, lv in enumerate(m.levels):
+        w = lv.width
+        for mip in range(lv.num_mips):
+            got = nb.bc1_decode_level(ctx, mat, i, mip).cpu().numpy()
+            want = oracle.bc1.decode_level(lv.blocks[mip], w, w)
+            assert np.array_equal(got, want), (i, mip)
+            w = max(4, w // 2)
+
+
+def test_decode_config0_full(nb, ctx):
+    wl = synth.decode_workload(0)
+    mat = nb.Material.from_synth(wl.material)
+    y = nb.decode(ctx, mat, grid=(256, 256))
+    ctx.sync()
+    ref = oracle.decode.decode_grid(wl.material, 256, 256)
+    assert max_abs(y.cpu().numpy(), ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("gw,gh", [(200, 136), (333, 3), (1, 1), (4, 1), (129, 65)])
+def test_decode_ragged_grids(nb, ctx, gw, gh):
+    wl = synth.decode_workload(0)
+    mat = nb.Material.from_synth(wl.material)
+    y = nb.decode(ctx, mat, grid=(gw, gh))
+    ctx.sync()
+    ref = oracle.decode.decode_grid(wl.material, gw, gh)
+    assert max_abs(y.cpu().numpy(), ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("address", ["clamp", "wrap"])
+def test_decode_uv_list(nb, ctx, address):
+    wl = synth.small_decode_workload(128, [12, 64, 64, 9], seed=77, address=address)
+    mat = nb.Material.from_synth(wl.material)
+    uv = synth.random_uv(78, 20001, lo=-0.5, hi=1.5)
+    y = nb.decode(ctx, mat, uv=torch.from_numpy(uv).cuda())
+    ctx.sync()
+    ref = oracle.decode.decode_uv(wl.material, uv)
+    assert max_abs(y.cpu().numpy(), ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("dims", [[12, 16, 9], [12, 32, 9], [12, 64, 9], [12, 32, 32, 9], [12, 64, 64, 64, 9]])
+def test_decode_mlp_shapes(nb, ctx, dims):
+    wl = synth.small_decode_workload(256, dims, seed=90 + len(dims) + dims[1])
+    mat = nb.Material.from_synth(wl.material)
+    y = nb.decode(ctx, mat, grid=(256, 96))
+    ctx.sync()
+    ref = oracle.decode.decode_grid(wl.material, 256, 96)
+    assert max_abs(y.cpu().numpy(), ref) <= TOL_FP32
+
+
+def test_decode_config1_full_size_sampled(nb, ctx):
+    """The 4096^2 decode in the launch configuration the benchmark times, checked
+    on 65,536 random texels plus the first and last rows and columns."""
+    wl = synth.decode_workload(1)
+    mat = nb.Material.from_synth(wl.material)
+    y = nb.decode(ctx, mat, grid=(4096, 4096))
+    ctx.sync()
+    rng = np.random.default_rng(5)
+    idx = np.concatenate([rng.integers(0, 4096 * 4096, 65536), np.arange(4096), 4096 * 4095 + np.arange(4096),
+                          np.arange(4096) * 4096, np.arange(4096) * 4096 + 4095])
+    ref = oracle.decode.decode_grid(wl.material, 4096, 4096, idx)
+    got = y[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert max_abs(got, ref) <= TOL_FP32
+    assert torch.isfinite(y).all()
+
+
+def test_zero_and_one_texel(nb, ctx):
+    wl = synth.decode_workload(0)
+    mat = nb.Material.from_synth(wl.material)
+    empty = torch.empty((0, 2), dtype=torch.float32, device="cuda")
+    y = nb.decode(ctx, mat, uv=empty)
+    assert y.shape == (0, 9)
+    uv = np.array([[0.3, 0.7]], dtype=np.float32)
+    y = nb.decode(ctx, mat, uv=torch.from_numpy(uv).cuda())
+    ctx.sync()
+    assert max_abs(y.cpu().numpy(), oracle.decode.decode_uv(wl.material, uv)) <= TOL_FP32
+
+
+def test_nan_weights_propagate(nb, ctx):
+    wl = synth.decode_workload(0)
+    wl.material.mlp.weights[2] = wl.material.mlp.weights[2].copy()
+    wl.material.mlp.weights[2][3, 5] = np.nan
+    mat = nb.Material.from_synth(wl.material)
+    y = nb.decode(ctx, mat, grid=(64, 64))
+    ctx.sync()
+    assert torch.isnan(y[:, 3]).any() and torch.isfinite(y[:, 0]).all()
+
+
+def test_invalid_arguments(nb, ctx):
+    from paper_2506_06040_gb300 import _abi
+    wl = synth.decode_workload(0)
+    mat = nb.Material.from_synth(wl.material)
+    with pytest.raises(nb.NbtcError) as e:
+        nb.decode(ctx, mat, grid=(64, 64), out=torch.empty((100, 9), device="cuda")[1:])  # misaligned
+    assert e.value.code == _abi.ERR_INVALID_ARG
+    mat.level_meta[0] = (66, 64, 1, 0.0)  # not a multiple of 4
+    with pytest.raises(nb.NbtcError) as e:
+        nb.decode(ctx, mat, grid=(8, 8))
+    assert e.value.code == _abi.ERR_INVALID_ARG
+    ctx.sync()
