@@ -154,6 +154,59 @@ def _max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def _time_steps(step, steps: int, warmup: int, flush, stream) -> list:
+    """CUDA-event time of each of `steps` calls of step() after `warmup` calls; the
+    L2 is flushed (a 256 MB write) before every timed call, outside its events."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 255)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_forms(args, nb, ctx, stream, flush, peaks, sm_count) -> dict:
+    """Precision forms on the 4096^2, 12-64-64-64-9 workload: FP32 SIMT, FP16 and
+    FP8 E4M3 on tcgen05.  Error = per-channel max |form - FP32 form| over the whole
+    texture (the FP32 form is within 1e-5 of the FP64 oracle in the parity tests)."""
+    import torch
+    wl = synth.decode_workload(2)
+    mat = nb.Material.from_synth(wl.material)
+    W = H = 4096
+    n = W * H
+    flop = 2 * (12 * 64 + 64 * 64 * 2 + 64 * 9)  # 19,072 per texel
+    out32 = torch.empty((n, 9), dtype=torch.float32, device="cuda")
+    out16 = torch.empty((n, 9), dtype=torch.float16, device="cuda")
+    res = {"workload": "decode-4096sq-bc1x4-mlp12-64-64-64-9", "flop_per_texel": flop}
+    t32 = _time_steps(lambda: nb.decode(ctx, mat, nb.FP32, grid=(W, H), out=out32, stream=stream),
+                      max(3, args.steps // 4), 2, flush, stream)
+    ms = statistics.mean(t32)
+    res["fp32"] = {"gtexel_s": n / ms / 1e6, "kernel_ms": ms}
+    packed16 = nb.pack_mlp(ctx, mat, nb.FP16, stream=stream)
+    absmax = nb.fp8_calibrate(ctx, mat, W, H, 16, stream=stream)
+    packed8 = nb.pack_mlp(ctx, mat, nb.FP8_E4M3, act_absmax=absmax, stream=stream)
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    for name, prec, packed, peak in (("fp16_tc", nb.FP16, packed16, bf16), ("fp8_tc", nb.FP8_E4M3, packed8, 2 * bf16)):
+        t = _time_steps(lambda: nb.decode(ctx, mat, prec, packed, grid=(W, H), out=out16, stream=stream),
+                        args.steps, args.warmup, flush, stream)
+        ms = statistics.mean(t)
+        err = (out16.float() - out32).abs().amax(dim=0).tolist()
+        ach = flop * n / (ms * 1e-3) / 1e12
+        res[name] = {"gtexel_s": n / ms / 1e6, "kernel_ms": ms, "max_abs_dev_vs_fp32_per_channel": err,
+                     "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": ach / peak,
+                                  "peak_source": "measured bf16 dense burst" + (" x 2 (fp8 nominal ratio)" if prec == nb.FP8_E4M3 else "")}}
+    res["fp16_tc_speedup_vs_fp32"] = res["fp16_tc"]["gtexel_s"] / res["fp32"]["gtexel_s"]
+    ctx.sync(stream)
+    return res
+
+
 def run_ours(args) -> dict | None:
     import torch
 
@@ -251,6 +304,8 @@ def run_ours(args) -> dict | None:
         "clocks": clk,
         "wall_s_timed": wall,
     }
+    if "forms" in args.parts:
+        res["forms"] = run_forms(args, nb, ctx, stream, flush, peaks, sm_count)
     ctx.close()
     if world > 1:
         import torch.distributed as dist
@@ -288,10 +343,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--parts", default="main,forms", help="comma list: main (always), forms")
     ap.add_argument("--side", type=int, default=4096, help="output side (4096 = the benchmark workload; "
                     "smaller sides are for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    args.parts = set(args.parts.split(","))
     if args.impl == "reference":
         res = run_reference(args)
     else:

@@ -166,7 +166,7 @@ nbtc_status nbtc_bc1_decode_level(nbtc_context* ctx, const nbtc_level* level, in
 
 static nbtc_status make_decode_args(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp,
                                     const float* uv, int64_t n, int32_t grid_w, int32_t grid_h,
-                                    void* out, DecodeArgs& a) {
+                                    void* out, DecodeArgs& a, bool need_out = true) {
   nbtc_status st;
   memset(&a, 0, sizeof(a));
   if ((st = check_mlp(mlp))) return st;
@@ -184,7 +184,7 @@ static nbtc_status make_decode_args(nbtc_context* ctx, const nbtc_latents* lat, 
   } else if (!aligned(uv, 8)) {
     return fail(NBTC_ERR_INVALID_ARG, "uv not 8-byte aligned");
   }
-  if (n > 0 && !out) return fail(NBTC_ERR_INVALID_ARG, "out is NULL");
+  if (need_out && !out) return fail(NBTC_ERR_INVALID_ARG, "out is NULL");
   if (out && !aligned(out, 16)) return fail(NBTC_ERR_INVALID_ARG, "out not 16-byte aligned");
   a.wrap = lat->address == NBTC_WRAP;
   a.uv = uv;
@@ -206,7 +206,8 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
   if (step < 1) return fail(NBTC_ERR_INVALID_ARG, "step must be >= 1");
   if (!act_absmax_dev) return fail(NBTC_ERR_INVALID_ARG, "act_absmax is NULL");
   DecodeArgs a;
-  if ((st = make_decode_args(ctx, lat, mlp, nullptr, (int64_t)grid_w * grid_h, grid_w, grid_h, nullptr, a)))
+  if ((st = make_decode_args(ctx, lat, mlp, nullptr, (int64_t)grid_w * grid_h, grid_w, grid_h, nullptr, a,
+                             /*need_out=*/false)))
     return st;
   return launch_calibrate_fp32(ctx, a, mlp, step, act_absmax_dev, (cudaStream_t)stream);
 }
@@ -224,11 +225,10 @@ nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_m
       return launch_decode_fp32(ctx, a, mlp, (cudaStream_t)stream);
     case NBTC_FP16:
     case NBTC_FP8_E4M3:
-      return fail(NBTC_ERR_UNSUPPORTED, "tensor-core forms are not built yet");
+      return launch_decode_tc(ctx, a, mlp, precision, packed_dev, (cudaStream_t)stream);
     default:
       return fail(NBTC_ERR_INVALID_ARG, "unknown precision");
   }
-  (void)packed_dev;
 }
 
 nbtc_status nbtc_packed_mlp_bytes(const nbtc_mlp* mlp, int32_t precision, size_t* bytes) {
@@ -239,15 +239,19 @@ nbtc_status nbtc_packed_mlp_bytes(const nbtc_mlp* mlp, int32_t precision, size_t
     *bytes = 0;
     return NBTC_OK;
   }
-  return fail(NBTC_ERR_UNSUPPORTED, "tensor-core forms are not built yet");
+  if (precision != NBTC_FP16 && precision != NBTC_FP8_E4M3) return fail(NBTC_ERR_INVALID_ARG, "unknown precision");
+  return tc_packed_bytes(mlp, precision, bytes);
 }
 
 nbtc_status nbtc_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int32_t precision,
                           const float* act_absmax_dev, void* packed_dev, size_t packed_bytes,
                           void* stream) {
-  (void)ctx; (void)mlp; (void)precision; (void)act_absmax_dev; (void)packed_dev; (void)packed_bytes;
-  (void)stream;
-  return fail(NBTC_ERR_UNSUPPORTED, "tensor-core forms are not built yet");
+  nbtc_status st = enter(ctx);
+  if (st) return st;
+  if ((st = check_mlp(mlp))) return st;
+  if (precision != NBTC_FP16 && precision != NBTC_FP8_E4M3)
+    return fail(NBTC_ERR_INVALID_ARG, "pack_mlp takes NBTC_FP16 or NBTC_FP8_E4M3");
+  return launch_pack_mlp(ctx, mlp, precision, act_absmax_dev, packed_dev, packed_bytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"

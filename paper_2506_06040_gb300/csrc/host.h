@@ -39,6 +39,11 @@ inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_
 nbtc_status launch_bc1_decode(nbtc_context* ctx, const LevelView& v, uint8_t* out, cudaStream_t s);
 nbtc_status launch_decode_fp32(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp,
                                cudaStream_t s);
+nbtc_status tc_packed_bytes(const nbtc_mlp* mlp, int precision, size_t* bytes);
+nbtc_status launch_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int precision, const float* act_absmax,
+                            void* packed, size_t packed_bytes, cudaStream_t s);
+nbtc_status launch_decode_tc(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, int precision,
+                             const void* packed, cudaStream_t s);
 nbtc_status launch_calibrate_fp32(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp,
                                   int step, float* absmax, cudaStream_t s);
 
