@@ -178,12 +178,12 @@ def run_forms(args, nb, ctx, stream, flush, peaks, sm_count) -> dict:
     import torch
     wl = synth.decode_workload(2)
     mat = nb.Material.from_synth(wl.material)
-    W = H = 4096
+    W = H = args.form_side
     n = W * H
     flop = 2 * (12 * 64 + 64 * 64 * 2 + 64 * 9)  # 19,072 per texel
     out32 = torch.empty((n, 9), dtype=torch.float32, device="cuda")
     out16 = torch.empty((n, 9), dtype=torch.float16, device="cuda")
-    res = {"workload": "decode-4096sq-bc1x4-mlp12-64-64-64-9", "flop_per_texel": flop}
+    res = {"workload": f"decode-{W}sq-bc1x4-mlp12-64-64-64-9", "flop_per_texel": flop}
     t32 = _time_steps(lambda: nb.decode(ctx, mat, nb.FP32, grid=(W, H), out=out32, stream=stream),
                       max(3, args.steps // 4), 2, flush, stream)
     ms = statistics.mean(t32)
@@ -344,6 +344,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--parts", default="main,forms", help="comma list: main (always), forms")
+    ap.add_argument("--form-side", type=int, default=4096, help="output side of the precision-form workload")
     ap.add_argument("--side", type=int, default=4096, help="output side (4096 = the benchmark workload; "
                     "smaller sides are for profiling captures)")
     args = ap.parse_args()

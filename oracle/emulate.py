@@ -6,7 +6,11 @@ exactly the same operands the kernels round -- the 12 input features, every
 weight, every hidden activation after ReLU, and the final output -- with the
 conversions of `quant` (written from the format definitions), but accumulates
 each dot product exactly (FP64; products of FP16 / E4M3 values are exact in
-FP64 and the sums carry at most a 2^-53 relative error).  Bias is added in FP64.
+FP64 and the sums carry at most a 2^-53 relative error).
+
+Bias: the FP16 form feeds the bias to the tensor core like a weight (a column
+of ones in A, the bias in B), so the bias is an FP16 operand too and is rounded
+here; the FP8 form adds the FP32 bias in its FP32 epilogue, added here in FP64.
 
 It therefore separates the error that the precision itself costs (emulator vs
 FP64 oracle) from the error of the kernel's arithmetic (kernel vs emulator:
@@ -35,7 +39,7 @@ def forward_fp16(x: np.ndarray, weights: list, biases: list, round_output: bool 
     n = len(weights)
     for l, (w, b) in enumerate(zip(weights, biases)):
         w16 = quant.round_fp16(np.asarray(w, dtype=np.float64))
-        z = h @ w16.T + np.asarray(b, dtype=np.float64)
+        z = h @ w16.T + quant.round_fp16(np.asarray(b, dtype=np.float64))
         if l < n - 1:
             h = quant.round_fp16(np.maximum(z, 0.0))
         else:

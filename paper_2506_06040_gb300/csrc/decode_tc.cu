@@ -19,25 +19,31 @@ namespace nbtc {
 
 using namespace sm100;
 
-constexpr int kGroups = 4;           // tile groups per CTA
 constexpr int kTile = 128;           // texels per tile = MMA M
 constexpr int kHid = 64;             // hidden width of the tensor-core forms
 constexpr int kOutPad = 16;          // output layer N (channels padded)
 constexpr int kMaxOut = 16;
 
 // Byte layout of a packed MLP (identical in global memory and shared memory).
+// FP16: every layer's bias enters the MMA as an FP16 operand -- layer 1 through
+// K column 12 of W1 (A0 carries a 1 there), later layers through a small
+// [N x 16] bias tile multiplied by a tile of ones.  FP8: the FP32 bias and the
+// per-layer scale are applied in the epilogue.
 struct TcLayout {
   int nhid;   // hidden layers (1..3)
   bool fp8;
   __host__ __device__ int esz() const { return fp8 ? 1 : 2; }
-  __host__ __device__ int w1_bytes() const { return 2048; }                     // 64 x K1 (16 f16 / 32 e4m3)
-  __host__ __device__ int wh_bytes() const { return kHid * kHid * esz(); }      // 64 x 64
+  __host__ __device__ int wh_bytes() const { return kHid * kHid * esz(); }   // 64 x 64
+  __host__ __device__ int bth_bytes() const { return fp8 ? 0 : kHid * 16 * 2; }   // 64 x 16 bias tile
   __host__ __device__ int wo_bytes() const { return kOutPad * kHid * esz(); }   // 16 x 64
-  __host__ __device__ int off_w1() const { return 0; }
-  __host__ __device__ int off_wh(int l) const { return 2048 + l * wh_bytes(); }  // l = 0 .. nhid-2
-  __host__ __device__ int off_wo() const { return 2048 + (nhid - 1) * wh_bytes(); }
-  __host__ __device__ int off_bias() const { return off_wo() + wo_bytes(); }    // nhid*64 + 16 floats
-  __host__ __device__ int off_alpha() const { return off_bias() + (nhid * kHid + kOutPad) * 4; }  // nhid+2 floats
+  __host__ __device__ int bto_bytes() const { return fp8 ? 0 : kOutPad * 16 * 2; }  // 16 x 16 bias tile
+  __host__ __device__ int off_w1() const { return 0; }                                // 64 x K1: 2048 B
+  __host__ __device__ int off_wh(int l) const { return 2048 + l * (wh_bytes() + bth_bytes()); }  // l < nhid-1
+  __host__ __device__ int off_bth(int l) const { return off_wh(l) + wh_bytes(); }
+  __host__ __device__ int off_wo() const { return off_wh(nhid - 1); }
+  __host__ __device__ int off_bto() const { return off_wo() + wo_bytes(); }
+  __host__ __device__ int off_bias() const { return off_bto() + bto_bytes(); }    // nhid*64 + 16 floats
+  __host__ __device__ int off_alpha() const { return off_bias() + (nhid * kHid + kOutPad) * 4; }  // 8 floats
   __host__ __device__ int bytes() const { return (off_alpha() + 8 * 4 + 15) & ~15; }
 };
 
@@ -65,56 +71,69 @@ struct TcArgs {
   long long budget;    // polls per bounded wait
 };
 
-// Shared-memory plan of the kernel.
+// Shared-memory plan.  Per group: A0 (128 x K1 operand, reused as the output
+// staging buffer) and Ah (128 x 64 operand, reused as the feature stage's
+// column buffer while no MMA reads it).
 struct TcSmem {
-  int image;       // packed MLP
+  int image;       // packed MLP (rounded to 1 KB)
+  int ones;        // 128 x 16 FP16 tile of ones in column 0
+  int groups;      // first group
   int group;       // bytes per group
-  int a0, ah, col, stage, bars;  // offsets inside a group
+  int a0, ah, bar; // offsets inside a group
+  int misc;        // weight barrier + TMEM slot
   int total;
 };
 
-__host__ __device__ inline TcSmem tc_smem(const TcLayout& L) {
+__host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int kGroups) {
   TcSmem s;
   s.image = (L.bytes() + 1023) & ~1023;
-  s.a0 = 0;                                  // 128 x K1 operand: 4 KB
-  s.ah = 4096;                               // 128 x 64 operand: 16 KB (f16) / 8 KB (e4m3)
-  s.col = s.ah + 16384;                      // 4 x kColCap float4
-  s.stage = s.col + 4 * kColCap * 16;        // 128 x 16 x 2 bytes of output staging
-  s.bars = s.stage + kTile * kMaxOut * 2;    // mbarrier
-  s.group = (s.bars + 16 + 1023) & ~1023;
-  s.total = s.image + kGroups * s.group + 64 /* weight barrier + TMEM slot */ + 1024 /* alignment slack */;
+  s.ones = s.image;
+  s.groups = s.ones + 4096;
+  s.a0 = 0;
+  s.ah = 4096;
+  s.bar = s.ah + 16384;
+  s.group = (s.bar + 16 + 1023) & ~1023;
+  s.misc = s.groups + kGroups * s.group;
+  s.total = s.misc + 64 + 1024 /* alignment slack */;
   return s;
 }
 
-template <int NHID, bool FP8>
+// kGroups tile groups of 128 threads per CTA, one CTA per SM.
+template <int NHID, bool FP8, int kGroups>
 __global__ void __launch_bounds__(kGroups * kTile, 1) k_decode_tc(TcArgs p) {
   constexpr TcLayout L{NHID, FP8};
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const TcSmem S = tc_smem(L);
+  const TcSmem S = tc_smem(L, kGroups);
   const uint32_t sbase = smem_u32(smem);
   const int tid = threadIdx.x;
   const int g = tid / kTile;          // group
   const int gt = tid % kTile;         // texel row inside the tile
   const int warp = tid / 32;
   const bool leader = gt == 0;
-  unsigned char* gsm = smem + S.image + g * S.group;
-  const uint32_t gbase = sbase + S.image + g * S.group;
-  const uint32_t wbar = sbase + S.image + kGroups * S.group;       // weight-load barrier
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S.image + kGroups * S.group + 16);
-  const uint32_t gbar = gbase + S.bars;
+  unsigned char* gsm = smem + S.groups + g * S.group;
+  const uint32_t gbase = sbase + S.groups + g * S.group;
+  const uint32_t wbar = sbase + S.misc;                                  // weight-load barrier
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S.misc + 16);
+  const uint32_t gbar = gbase + S.bar;
   const int bar_id = 1 + g;
+  constexpr uint32_t kTmemCols = kGroups * kHid <= 256 ? 256 : 512;
 
   if (warp == 0) {
-    tmem_alloc(smem_u32(tmem_slot), kGroups * kHid);
+    tmem_alloc(smem_u32(tmem_slot), kTmemCols);
     tmem_relinquish();
   }
   if (tid == 0) {
     mbar_init(wbar, 1);
-    for (int q = 0; q < kGroups; ++q) mbar_init(sbase + S.image + q * S.group + S.bars, 1);
+    for (int q = 0; q < kGroups; ++q) mbar_init(sbase + S.groups + q * S.group + S.bar, 1);
     fence_mbar_init();
     mbar_expect_tx(wbar, (uint32_t)L.bytes());
     bulk_g2s(sbase, p.packed, (uint32_t)L.bytes(), wbar);
+  }
+  if (!FP8 && tid < kTile) {  // ones tile: column 0 = 1.0 (FP16), rest 0
+    sts128(sbase + S.ones + off_interleave(tid, 0), 0x3C00u, 0u, 0u, 0u);
+    sts128(sbase + S.ones + off_interleave(tid, 16), 0u, 0u, 0u, 0u);
+    fence_proxy_async_smem();
   }
   tc_fence_before();
   __syncthreads();
@@ -128,8 +147,8 @@ __global__ void __launch_bounds__(kGroups * kTile, 1) k_decode_tc(TcArgs p) {
   const float* bias = reinterpret_cast<const float*>(smem + L.off_bias());
   const float* alpha = reinterpret_cast<const float*>(smem + L.off_alpha());
   const uint32_t a0 = gbase + S.a0, ah = gbase + S.ah;
-  float4* colbuf = reinterpret_cast<float4*>(gsm + S.col);
-  uint16_t* stage = reinterpret_cast<uint16_t*>(gsm + S.stage);
+  float4* colbuf = reinterpret_cast<float4*>(gsm + S.ah);
+  uint16_t* stage = reinterpret_cast<uint16_t*>(gsm + S.a0);
   constexpr uint32_t ID_HID = idesc(0, kTile, kHid);
   constexpr uint32_t ID_OUT = idesc(0, kTile, kOutPad);
   uint32_t phase = 0;
@@ -139,21 +158,22 @@ __global__ void __launch_bounds__(kGroups * kTile, 1) k_decode_tc(TcArgs p) {
     const int64_t t0 = tile * kTile;
     const int64_t tex = t0 + gt;
     const bool full = t0 + kTile <= p.d.n;
-    if (leader) bulk_wait_read0();  // previous tile's staged output has been read
+    if (leader) bulk_wait_read0();  // the previous tile's staged output (in A0) has been read
 
     // ---- features -> A0
     float f[12];
     if (p.footprint) {
-      footprint_features<kTile>(p.d, t0, gt, colbuf, bar_id, f);
+      footprint_features<kTile>(p.d, t0, gt, colbuf, bar_id, f);  // includes a group barrier
     } else {
       direct_features(p.d, tex < p.d.n ? tex : p.d.n - 1, f);
+      named_bar_sync(bar_id, kTile);
     }
     if constexpr (!FP8) {
       const uint32_t w0 = cvt_f16x2(f[0], f[1]), w1 = cvt_f16x2(f[2], f[3]);
       const uint32_t w2 = cvt_f16x2(f[4], f[5]), w3 = cvt_f16x2(f[6], f[7]);
       const uint32_t w4 = cvt_f16x2(f[8], f[9]), w5 = cvt_f16x2(f[10], f[11]);
       sts128(a0 + off_interleave(gt, 0), w0, w1, w2, w3);
-      sts128(a0 + off_interleave(gt, 16), w4, w5, 0u, 0u);
+      sts128(a0 + off_interleave(gt, 16), w4, w5, 0x3C00u /* k = 12: 1.0 for the bias */, 0u);
     } else {
       const float is = alpha[NHID + 1];  // 1 / input scale
       uint32_t q[3];
@@ -168,6 +188,7 @@ __global__ void __launch_bounds__(kGroups * kTile, 1) k_decode_tc(TcArgs p) {
     tc_fence_before();
     named_bar_sync(bar_id, kTile);
 
+#pragma unroll 1
     for (int layer = 0; layer <= NHID; ++layer) {
       const bool last = layer == NHID;
       // ---- issue this layer's MMAs
@@ -187,54 +208,56 @@ __global__ void __launch_bounds__(kGroups * kTile, 1) k_decode_tc(TcArgs p) {
               mma_f8(tmem, smem_desc(ah + kk * 32, 16, 512, kSwz64), smem_desc(wb + kk * 32, 16, 512, kSwz64), id,
                      kk > 0);
           } else {
+            const uint32_t bt = sbase + (last ? L.off_bto() : L.off_bth(layer - 1));
+            mma_f16(tmem, smem_desc(sbase + S.ones, 128, 256, kSwzNone), smem_desc(bt, 128, 256, kSwzNone), id, 0);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
               mma_f16(tmem, smem_desc(ah + kk * 32, 16, 1024, kSwz128), smem_desc(wb + kk * 32, 16, 1024, kSwz128),
-                      id, kk > 0);
+                      id, 1);
           }
         }
         mma_commit(gbar);
       }
-      // ---- wait for the accumulator
-      // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
+      // ---- wait for the accumulator (warp-uniform: tcgen05.ld is a .sync.aligned warp instruction)
       const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(gbar, phase, p.budget));
       phase ^= 1u;
       tc_fence_after();
-      const float alp = alpha[layer];
       if (!last) {
-        uint32_t r[64];
-        if (ok) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) tmem_ld16(tmem_row + 16 * c, r + 16 * c);
-          tmem_wait_ld64(r);
-        }
+        const float alp = alpha[layer];
         const float* b = bias + layer * kHid;
-        if constexpr (!FP8) {
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int j = 8 * c + 2 * e;
-              w[e] = cvt_relu_f16x2(fmaf(__uint_as_float(r[j]), alp, b[j]),
-                                    fmaf(__uint_as_float(r[j + 1]), alp, b[j + 1]));
-            }
-            sts128(ah + off_sw128(gt, 16 * c), w[0], w[1], w[2], w[3]);
+        for (int half = 0; half < 2; ++half) {
+          uint32_t r[32];
+          if (ok) {
+            tmem_ld16(tmem_row + 32 * half, r);
+            tmem_ld16(tmem_row + 32 * half + 16, r + 16);
+            tmem_wait_ld32(r);
           }
-        } else {
+          if constexpr (!FP8) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int j = 16 * c + 4 * e;
-              w[e] = (uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j]), alp, b[j]),
-                                               fmaf(__uint_as_float(r[j + 1]), alp, b[j + 1])) |
-                     ((uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j + 2]), alp, b[j + 2]),
-                                                fmaf(__uint_as_float(r[j + 3]), alp, b[j + 3]))
-                      << 16);
+            for (int c = 0; c < 4; ++c) {
+              const int j = 8 * c;
+              sts128(ah + off_sw128(gt, 16 * (4 * half + c)),
+                     cvt_relu_f16x2(__uint_as_float(r[j + 0]), __uint_as_float(r[j + 1])),
+                     cvt_relu_f16x2(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])),
+                     cvt_relu_f16x2(__uint_as_float(r[j + 4]), __uint_as_float(r[j + 5])),
+                     cvt_relu_f16x2(__uint_as_float(r[j + 6]), __uint_as_float(r[j + 7])));
             }
-            sts128(ah + off_sw64(gt, 16 * c), w[0], w[1], w[2], w[3]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              uint32_t w[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int j = 16 * c + 4 * e, jj = 32 * half + j;
+                w[e] = (uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j]), alp, b[jj]),
+                                                 fmaf(__uint_as_float(r[j + 1]), alp, b[jj + 1])) |
+                       ((uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j + 2]), alp, b[jj + 2]),
+                                                  fmaf(__uint_as_float(r[j + 3]), alp, b[jj + 3]))
+                        << 16);
+              }
+              sts128(ah + off_sw64(gt, 16 * (2 * half + c)), w[0], w[1], w[2], w[3]);
+            }
           }
         }
         fence_proxy_async_smem();
@@ -247,10 +270,12 @@ __global__ void __launch_bounds__(kGroups * kTile, 1) k_decode_tc(TcArgs p) {
           tmem_ld16(tmem_row, r);
           tmem_wait_ld16(r);
         }
+        const float alp = alpha[NHID];
         const float* b = bias + NHID * kHid;
         __half hv[kMaxOut];
 #pragma unroll
-        for (int k = 0; k < kMaxOut; ++k) hv[k] = __float2half_rn(fmaf(__uint_as_float(r[k]), alp, b[k]));
+        for (int k = 0; k < kMaxOut; ++k)
+          hv[k] = FP8 ? __float2half_rn(fmaf(__uint_as_float(r[k]), alp, b[k])) : __float2half_rn(__uint_as_float(r[k]));
         if (full) {
 #pragma unroll
           for (int k = 0; k < kMaxOut; ++k)
@@ -265,8 +290,7 @@ __global__ void __launch_bounds__(kGroups * kTile, 1) k_decode_tc(TcArgs p) {
         tc_fence_before();
         failed = named_bar_or(bar_id, kTile, !ok);
         if (!failed && full && leader) {
-          bulk_s2g(reinterpret_cast<uint16_t*>(p.d.out) + t0 * p.nout, gbase + S.stage,
-                   (uint32_t)(kTile * p.nout * 2));
+          bulk_s2g(reinterpret_cast<uint16_t*>(p.d.out) + t0 * p.nout, gbase + S.a0, (uint32_t)(kTile * p.nout * 2));
           bulk_commit();
         }
       }
@@ -277,7 +301,7 @@ __global__ void __launch_bounds__(kGroups * kTile, 1) k_decode_tc(TcArgs p) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(*tmem_slot, kGroups * kHid);
+  if (warp == 0) tmem_dealloc(*tmem_slot, kTmemCols);
 }
 
 // ------------------------------------------------------------------ packing
@@ -340,6 +364,20 @@ __global__ void k_pack_mlp(const float* __restrict__ W, const float* __restrict_
     }
     off += in * o;
   }
+  if (!fp8) {  // FP16 biases as MMA operands: W1 column 12, then [N x 16] tiles (column 0)
+    int bo = 0;
+    for (int l = 0; l < nl; ++l) {
+      const int o = l == nhid ? nout : kHid;
+      for (int e = threadIdx.x; e < o; e += blockDim.x) {
+        uint32_t dst;
+        if (l == 0) dst = L.off_w1() + off_interleave(e, 2 * nin);
+        else if (l == nhid) dst = L.off_bto() + off_interleave(e, 0);
+        else dst = L.off_bth(l - 1) + off_interleave(e, 0);
+        *reinterpret_cast<__half*>(out + dst) = __float2half_rn(B[bo + e]);
+      }
+      bo += o;
+    }
+  }
   // biases (hidden layers pre-divided by the next layer's input scale) and epilogue multipliers
   float* bias = reinterpret_cast<float*>(out + L.off_bias());
   float* alpha = reinterpret_cast<float*>(out + L.off_alpha());
@@ -396,10 +434,10 @@ nbtc_status launch_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int precisio
   return cuda_check(cudaGetLastError(), "launch k_pack_mlp");
 }
 
-template <int NHID, bool FP8>
-static nbtc_status launch_tc_t(nbtc_context* ctx, const TcArgs& p, cudaStream_t s) {
-  const TcSmem S = tc_smem(TcLayout{NHID, FP8});
-  auto kern = k_decode_tc<NHID, FP8>;
+template <int NHID, bool FP8, int kGroups>
+static nbtc_status launch_tc_g(nbtc_context* ctx, const TcArgs& p, cudaStream_t s) {
+  const TcSmem S = tc_smem(TcLayout{NHID, FP8}, kGroups);
+  auto kern = k_decode_tc<NHID, FP8, kGroups>;
   nbtc_status st =
       cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S.total), "smem attribute");
   if (st) return st;
@@ -407,6 +445,11 @@ static nbtc_status launch_tc_t(nbtc_context* ctx, const TcArgs& p, cudaStream_t 
   if (grid > ctx->sm_count) grid = ctx->sm_count;
   kern<<<(int)grid, kGroups * kTile, S.total, s>>>(p);
   return cuda_check(cudaGetLastError(), "launch k_decode_tc");
+}
+
+template <int NHID, bool FP8>
+static nbtc_status launch_tc_t(nbtc_context* ctx, const TcArgs& p, cudaStream_t s) {
+  return ctx->tc_groups == 6 ? launch_tc_g<NHID, FP8, 6>(ctx, p, s) : launch_tc_g<NHID, FP8, 4>(ctx, p, s);
 }
 
 nbtc_status launch_decode_tc(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, int precision,

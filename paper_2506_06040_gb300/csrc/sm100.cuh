@@ -127,6 +127,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
 __device__ __forceinline__ void tmem_wait_ld16(uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" : NBTC_W16(0)::"memory");
 }
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : NBTC_W16(0), NBTC_W16(16)::"memory");
+}
 __device__ __forceinline__ void tmem_wait_ld64(uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" : NBTC_W16(0), NBTC_W16(16) ::"memory");
   asm volatile("" : NBTC_W16(32), NBTC_W16(48)::"memory");

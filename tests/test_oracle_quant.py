@@ -125,3 +125,12 @@ def test_fp8_emulator_rounds_operands():
     ref = mlp.forward(x, ws, bs)
     err = np.abs(emu - ref)
     assert 1e-3 < err.max() < 0.5 and err.mean() < 0.05
+
+
+def test_fp16_emulator_rounds_bias_as_operand():
+    """The FP16 form's bias is an FP16 operand: 1 + 2^-12 rounds to 1."""
+    ws = [np.zeros((2, 3)), np.zeros((1, 2))]
+    bs = [np.array([0.5, 1.0 + 2.0 ** -12]), np.array([1.0 + 2.0 ** -12])]
+    x = np.ones((1, 3))
+    np.testing.assert_array_equal(emulate.forward_fp16(x, ws, bs, round_output=False), [[1.0]])
+    np.testing.assert_array_equal(mlp.forward(x, ws, bs), [[1.0 + 2.0 ** -12]])
