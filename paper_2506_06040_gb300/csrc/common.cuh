@@ -139,8 +139,15 @@ struct DecodeArgs {
 // uv of output texel t.
 __device__ __forceinline__ float2 texel_uv(const DecodeArgs& a, int64_t t) {
   if (a.uv) return __ldg(reinterpret_cast<const float2*>(a.uv) + t);
-  const int64_t j = t / a.grid_w;
-  const int64_t i = t - j * a.grid_w;
+  int64_t j, i;
+  if (a.n <= 0xFFFFFFFFll) {  // 32-bit division when the grid allows it
+    const uint32_t tj = (uint32_t)t / (uint32_t)a.grid_w;
+    j = tj;
+    i = (uint32_t)t - tj * (uint32_t)a.grid_w;
+  } else {
+    j = t / a.grid_w;
+    i = t - j * a.grid_w;
+  }
   return make_float2(((float)i + 0.5f) * a.inv_gw, ((float)j + 0.5f) * a.inv_gh);
 }
 
