@@ -174,6 +174,63 @@ nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_m
                         int32_t precision, const void* packed_dev, const float* uv_dev,
                         int64_t n, int32_t grid_w, int32_t grid_h, void* out_dev, void* stream);
 
+/* ------------------------------------------------------------------ training
+ *
+ * One optimisation step of the decoder on continuous latents (Sec. 3.2: the
+ * compressor's texture-unit replica, gradients through the MLP into every
+ * latent texel, Adam with lr 1e-3 for the MLP and 1e-2 for the latents).  The
+ * latents here are plain FP32 textures (before BC1 quantisation): level k is
+ * latents[k] = [heights[k]][widths[k]][3], sampled bilinearly with clamp
+ * addressing and the level's shift.  The MLP is [12, 64, 64, C] (C <= 16) in the
+ * nbtc_mlp layout.  The target is [target_h][target_w][C] FP32, sampled
+ * bilinearly (clamp, no shift) at the same uv.  Loss: mean over batch and
+ * channels of (y - t)^2 (NBTC_LOSS_MSE) or |y - t| (NBTC_LOSS_L1).
+ *
+ * Gradient sums over the batch use compensated (Neumaier) FP32 summation;
+ * latent gradients are accumulated with FP32 atomics (their summation order
+ * varies between runs).  Adam follows the PyTorch form with bias correction:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ */
+typedef struct {
+  int32_t num_levels;                       /* 4 */
+  int32_t widths[NBTC_MAX_LEVELS], heights[NBTC_MAX_LEVELS];
+  float shifts[NBTC_MAX_LEVELS];
+  float* latents[NBTC_MAX_LEVELS];          /* updated in place by nbtc_train_step */
+  float* latent_grads[NBTC_MAX_LEVELS];     /* overwritten with this batch's gradient */
+  float* latent_m[NBTC_MAX_LEVELS];         /* Adam moments (train step only) */
+  float* latent_v[NBTC_MAX_LEVELS];
+  nbtc_mlp mlp;                             /* weights/biases updated in place by the step */
+  float* grad_w;                            /* overwritten: same layout as mlp.weights */
+  float* grad_b;                            /* overwritten: same layout as mlp.biases */
+  float* m_w; float* v_w; float* m_b; float* v_b;   /* Adam moments of the MLP */
+  const float* target;                      /* [target_h][target_w][C] (train step only) */
+  int32_t target_w, target_h;
+  const float* uv;                          /* [batch][2] */
+  int64_t batch;
+  int32_t step;                             /* Adam step number t of this update, >= 1 */
+  float lr_mlp, lr_latent, beta1, beta2, eps;
+  int32_t loss;                             /* nbtc_loss */
+  void* workspace;                          /* caller-owned scratch, 16-byte aligned */
+  size_t workspace_bytes;                   /* >= nbtc_train_workspace_bytes() */
+} nbtc_train_args;
+
+/* Scratch bytes the training calls need on this context's device. */
+nbtc_status nbtc_train_workspace_bytes(nbtc_context* ctx, const nbtc_train_args* args, size_t* bytes);
+
+/* Forward + loss + backward + Adam (MLP and latents) for one batch.  Writes
+ * the batch loss to loss_dev (one float), the gradients to grad_w / grad_b /
+ * latent_grads, and updates parameters and moments in place. */
+nbtc_status nbtc_train_step(nbtc_context* ctx, const nbtc_train_args* args, float* loss_dev, void* stream);
+
+/* Forward only: y_dev[batch][C] = f(latents sampled at uv). */
+nbtc_status nbtc_forward_continuous(nbtc_context* ctx, const nbtc_train_args* args, float* y_dev, void* stream);
+
+/* Backward only, from a given dL/dy (dy_dev[batch][C]): writes grad_w, grad_b
+ * and latent_grads (activations are recomputed, not stored); no update. */
+nbtc_status nbtc_backward_continuous(nbtc_context* ctx, const nbtc_train_args* args, const float* dy_dev,
+                                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

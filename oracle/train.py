@@ -77,10 +77,12 @@ def backward(dy: np.ndarray, cache: dict, latents: list, shifts, weights: list):
     dlat = []
     for k, (t, s) in enumerate(zip(latents, shifts)):
         h, w = t.shape[:2]
-        acc = np.zeros((h, w, 3))
+        acc = np.zeros(h * w * 3)
         for (yy, xx, wt) in _taps(h, w, cache["u"], cache["v"], s):
-            np.add.at(acc, (yy, xx), wt[:, None] * dx[:, 3 * k:3 * k + 3])
-        dlat.append(acc)
+            for c in range(3):
+                # dL/dT_k[texel, c] += tap weight * dL/dx_k,c  (weighted histogram over texels)
+                acc[c::3] += np.bincount(yy * w + xx, weights=wt * dx[:, 3 * k + c], minlength=h * w)
+        dlat.append(acc.reshape(h, w, 3))
     return dW, db, dlat
 
 

@@ -33,6 +33,18 @@ class Mlp(ctypes.Structure):
                 ("weights", c_void_p), ("biases", c_void_p)]
 
 
+class TrainArgs(ctypes.Structure):
+    _fields_ = [("num_levels", c_int32), ("widths", c_int32 * MAX_LEVELS), ("heights", c_int32 * MAX_LEVELS),
+                ("shifts", c_float * MAX_LEVELS), ("latents", c_void_p * MAX_LEVELS),
+                ("latent_grads", c_void_p * MAX_LEVELS), ("latent_m", c_void_p * MAX_LEVELS),
+                ("latent_v", c_void_p * MAX_LEVELS), ("mlp", Mlp), ("grad_w", c_void_p), ("grad_b", c_void_p),
+                ("m_w", c_void_p), ("v_w", c_void_p), ("m_b", c_void_p), ("v_b", c_void_p), ("target", c_void_p),
+                ("target_w", c_int32), ("target_h", c_int32), ("uv", c_void_p), ("batch", c_int64),
+                ("step", c_int32), ("lr_mlp", c_float), ("lr_latent", c_float), ("beta1", c_float),
+                ("beta2", c_float), ("eps", c_float), ("loss", c_int32), ("workspace", c_void_p),
+                ("workspace_bytes", c_size_t)]
+
+
 # name -> (restype, argtypes)
 PROTOTYPES = {
     "nbtc_create": (c_int, [c_int, POINTER(c_void_p)]),
@@ -48,6 +60,10 @@ PROTOTYPES = {
                                    c_void_p, c_void_p]),
     "nbtc_decode": (c_int, [c_void_p, POINTER(Latents), POINTER(Mlp), c_int32, c_void_p, c_void_p, c_int64,
                             c_int32, c_int32, c_void_p, c_void_p]),
+    "nbtc_train_workspace_bytes": (c_int, [c_void_p, POINTER(TrainArgs), POINTER(c_size_t)]),
+    "nbtc_train_step": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
+    "nbtc_forward_continuous": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
+    "nbtc_backward_continuous": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
 }
 
 _lib = None

@@ -256,4 +256,34 @@ nbtc_status nbtc_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int32_t precis
   return launch_pack_mlp(ctx, mlp, precision, act_absmax_dev, packed_dev, packed_bytes, (cudaStream_t)stream);
 }
 
+nbtc_status nbtc_train_workspace_bytes(nbtc_context* ctx, const nbtc_train_args* args, size_t* bytes) {
+  if (!ctx || !args || !bytes) return fail(NBTC_ERR_INVALID_ARG, "NULL argument");
+  *bytes = train_workspace(ctx, args);
+  return NBTC_OK;
+}
+
+nbtc_status nbtc_train_step(nbtc_context* ctx, const nbtc_train_args* args, float* loss_dev, void* stream) {
+  nbtc_status st = enter(ctx);
+  if (st) return st;
+  if (!args) return fail(NBTC_ERR_INVALID_ARG, "args NULL");
+  return train_step_impl(ctx, args, loss_dev, (cudaStream_t)stream, 2, nullptr, nullptr, args->workspace,
+                         args->workspace_bytes);
+}
+
+nbtc_status nbtc_forward_continuous(nbtc_context* ctx, const nbtc_train_args* args, float* y_dev, void* stream) {
+  nbtc_status st = enter(ctx);
+  if (st) return st;
+  if (!args) return fail(NBTC_ERR_INVALID_ARG, "args NULL");
+  return train_step_impl(ctx, args, nullptr, (cudaStream_t)stream, 0, nullptr, y_dev, nullptr, 0);
+}
+
+nbtc_status nbtc_backward_continuous(nbtc_context* ctx, const nbtc_train_args* args, const float* dy_dev,
+                                     void* stream) {
+  nbtc_status st = enter(ctx);
+  if (st) return st;
+  if (!args) return fail(NBTC_ERR_INVALID_ARG, "args NULL");
+  return train_step_impl(ctx, args, nullptr, (cudaStream_t)stream, 1, dy_dev, nullptr, args->workspace,
+                         args->workspace_bytes);
+}
+
 }  // extern "C"

@@ -45,6 +45,10 @@ nbtc_status launch_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int precisio
                             void* packed, size_t packed_bytes, cudaStream_t s);
 nbtc_status launch_decode_tc(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, int precision,
                              const void* packed, cudaStream_t s);
+size_t train_workspace(nbtc_context* ctx, const nbtc_train_args* A);
+// mode: 0 forward (y), 1 backward from dy, 2 full step (loss, grads, Adam)
+nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* loss, cudaStream_t s, int mode,
+                            const float* dy, float* y, void* workspace, size_t workspace_bytes);
 nbtc_status launch_calibrate_fp32(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp,
                                   int step, float* absmax, cudaStream_t s);
 

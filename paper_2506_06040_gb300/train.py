@@ -1,0 +1,134 @@
+"""Training on continuous latents through the C ABI (Sec. 3.2): the model's
+tensors live in torch device memory; every step of forward, loss, backward and
+Adam runs in the library's kernels."""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_size_t, c_void_p
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check
+
+
+def _p(t):
+    return c_void_p(0 if t is None else t.data_ptr())
+
+
+class ContinuousModel:
+    """Latent pyramid (4 FP32 textures [h, w, 3]) + MLP [12, 64, 64, C] with their
+    gradients and Adam moments, on one device."""
+
+    def __init__(self, latents, shifts, weights, biases, device="cuda"):
+        dev = torch.device(device)
+        self.device = dev
+        self.latents = [torch.as_tensor(np.ascontiguousarray(l, dtype=np.float32)).to(dev) for l in latents]
+        self.shifts = [float(s) for s in shifts]
+        self.dims = [int(weights[0].shape[1])] + [int(w.shape[0]) for w in weights]
+        self.weights = torch.from_numpy(np.concatenate([np.asarray(w, np.float32).ravel() for w in weights])).to(dev)
+        self.biases = torch.from_numpy(np.concatenate([np.asarray(b, np.float32).ravel() for b in biases])).to(dev)
+        z = torch.zeros_like
+        self.latent_grads = [z(l) for l in self.latents]
+        self.latent_m = [z(l) for l in self.latents]
+        self.latent_v = [z(l) for l in self.latents]
+        self.grad_w, self.grad_b = z(self.weights), z(self.biases)
+        self.m_w, self.v_w, self.m_b, self.v_b = z(self.weights), z(self.weights), z(self.biases), z(self.biases)
+        self.step_count = 0
+        self.workspace = None
+
+    @classmethod
+    def from_synth(cls, wl, device="cuda"):
+        return cls(wl.latents, wl.shifts, wl.mlp.weights, wl.mlp.biases, device)
+
+    def layer_slices(self):
+        """(weight, bias) offsets of each layer in the packed parameter vectors."""
+        out, wo, bo = [], 0, 0
+        for i in range(len(self.dims) - 1):
+            n_w, n_b = self.dims[i] * self.dims[i + 1], self.dims[i + 1]
+            out.append(((wo, wo + n_w), (bo, bo + n_b)))
+            wo += n_w
+            bo += n_b
+        return out
+
+    def args(self, uv, target=None, loss=_abi.LOSS_MSE, lr_mlp=1e-3, lr_latent=1e-2, betas=(0.9, 0.999),
+             eps=1e-8, latents=None, weights=None, biases=None) -> _abi.TrainArgs:
+        a = _abi.TrainArgs()
+        lats = latents if latents is not None else self.latents
+        a.num_levels = len(lats)
+        for k, l in enumerate(lats):
+            a.heights[k], a.widths[k] = int(l.shape[0]), int(l.shape[1])
+            a.shifts[k] = self.shifts[k]
+            a.latents[k] = l.data_ptr()
+            a.latent_grads[k] = self.latent_grads[k].data_ptr()
+            a.latent_m[k] = self.latent_m[k].data_ptr()
+            a.latent_v[k] = self.latent_v[k].data_ptr()
+        a.mlp.num_layers = len(self.dims) - 1
+        for i, d in enumerate(self.dims):
+            a.mlp.dims[i] = d
+        a.mlp.weights = (weights if weights is not None else self.weights).data_ptr()
+        a.mlp.biases = (biases if biases is not None else self.biases).data_ptr()
+        a.grad_w, a.grad_b = self.grad_w.data_ptr(), self.grad_b.data_ptr()
+        a.m_w, a.v_w, a.m_b, a.v_b = (self.m_w.data_ptr(), self.v_w.data_ptr(), self.m_b.data_ptr(),
+                                      self.v_b.data_ptr())
+        if target is not None:
+            a.target = target.data_ptr()
+            a.target_h, a.target_w = int(target.shape[0]), int(target.shape[1])
+        a.uv = 0 if uv is None or uv.numel() == 0 else uv.data_ptr()
+        a.batch = 0 if uv is None else int(uv.shape[0])
+        a.step = self.step_count + 1
+        a.lr_mlp, a.lr_latent = lr_mlp, lr_latent
+        a.beta1, a.beta2, a.eps = betas[0], betas[1], eps
+        a.loss = loss
+        return a
+
+    def _workspace(self, ctx, a):
+        n = c_size_t()
+        check(ctx.lib.nbtc_train_workspace_bytes(ctx.handle, byref(a), byref(n)))
+        if self.workspace is None or self.workspace.numel() < n.value:
+            self.workspace = torch.empty(max(n.value, 16), dtype=torch.uint8, device=self.device)
+        a.workspace, a.workspace_bytes = self.workspace.data_ptr(), self.workspace.numel()
+
+    def train_step(self, ctx, uv, target, loss=_abi.LOSS_MSE, stream=None, **kw) -> torch.Tensor:
+        """One full step; returns the batch loss as a device scalar."""
+        a = self.args(uv, target, loss, **kw)
+        self._workspace(ctx, a)
+        out = torch.empty(1, dtype=torch.float32, device=self.device)
+        s = c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+        check(ctx.lib.nbtc_train_step(ctx.handle, byref(a), _p(out), s))
+        self.step_count += 1
+        return out
+
+    def forward(self, ctx, uv, stream=None, **kw) -> torch.Tensor:
+        a = self.args(uv, **kw)
+        y = torch.empty((int(uv.shape[0]), self.dims[-1]), dtype=torch.float32, device=self.device)
+        s = c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+        check(ctx.lib.nbtc_forward_continuous(ctx.handle, byref(a), _p(y), s))
+        return y
+
+    def backward(self, ctx, uv, dy, stream=None, **kw):
+        """Gradients of sum(dy * y) into grad_w / grad_b / latent_grads."""
+        a = self.args(uv, **kw)
+        self._workspace(ctx, a)
+        s = c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+        check(ctx.lib.nbtc_backward_continuous(ctx.handle, byref(a), _p(dy), s))
+
+
+class NbtcDecodeFn(torch.autograd.Function):
+    """y = f(uv; latents, W, b): differentiable decode of continuous latents.
+    Forward and backward are the library's kernels (activations recomputed in
+    the backward, not stored)."""
+
+    @staticmethod
+    def forward(fctx, ctx, model, uv, lat0, lat1, lat2, lat3, weights, biases):
+        lats = [lat0.contiguous(), lat1.contiguous(), lat2.contiguous(), lat3.contiguous()]
+        w, b = weights.contiguous(), biases.contiguous()
+        fctx.saved = (ctx, model, uv, lats, w, b)
+        return model.forward(ctx, uv, latents=lats, weights=w, biases=b)
+
+    @staticmethod
+    def backward(fctx, dy):
+        ctx, model, uv, lats, w, b = fctx.saved
+        model.backward(ctx, uv, dy.contiguous().float(), latents=lats, weights=w, biases=b)
+        return (None, None, None, *[g.clone() for g in model.latent_grads], model.grad_w.clone(), model.grad_b.clone())

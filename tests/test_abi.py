@@ -48,6 +48,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(nbtc_level), offsetof(nbtc_level, width), offsetof(nbtc_level, shift),
          sizeof(nbtc_latents), offsetof(nbtc_latents, levels));
   printf("%zu %zu %zu\n", sizeof(nbtc_mlp), offsetof(nbtc_mlp, weights), offsetof(nbtc_mlp, biases));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(nbtc_train_args), offsetof(nbtc_train_args, mlp),
+         offsetof(nbtc_train_args, target_w), offsetof(nbtc_train_args, batch), offsetof(nbtc_train_args, loss),
+         offsetof(nbtc_train_args, workspace), offsetof(nbtc_train_args, workspace_bytes));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -59,7 +62,10 @@ int main(void) {
     got = [int(x) for x in out]
     want = [ctypes.sizeof(_abi.Level), _abi.Level.width.offset, _abi.Level.shift.offset,
             ctypes.sizeof(_abi.Latents), _abi.Latents.levels.offset,
-            ctypes.sizeof(_abi.Mlp), _abi.Mlp.weights.offset, _abi.Mlp.biases.offset]
+            ctypes.sizeof(_abi.Mlp), _abi.Mlp.weights.offset, _abi.Mlp.biases.offset,
+            ctypes.sizeof(_abi.TrainArgs), _abi.TrainArgs.mlp.offset, _abi.TrainArgs.target_w.offset,
+            _abi.TrainArgs.batch.offset, _abi.TrainArgs.loss.offset, _abi.TrainArgs.workspace.offset,
+            _abi.TrainArgs.workspace_bytes.offset]
     assert got == want
 
 

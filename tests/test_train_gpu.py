@@ -1,0 +1,162 @@
+"""GPU parity of the training path (continuous latents, Sec. 3.2) against the
+FP64 oracle: forward outputs, loss, MLP and latent gradients (relative error
+1e-4), and the Adam update; plus the autograd.Function."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def nb():
+    require_gpu()
+    import paper_2506_06040_gb300 as nb
+    return nb
+
+
+@pytest.fixture(scope="module")
+def ctx(nb):
+    c = nb.Context(0)
+    yield c
+    c.close()
+
+
+def _check_grad(got, ref, name):
+    got = np.asarray(got, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    nrm = np.linalg.norm(ref)
+    assert np.linalg.norm(got - ref) <= REL * nrm, (name, np.linalg.norm(got - ref) / nrm)
+    assert np.abs(got - ref).max() <= REL * np.abs(ref).max(), (name, np.abs(got - ref).max() / np.abs(ref).max())
+
+
+def kink_free(wl, uv, margin=1e-5):
+    """Drops samples with a hidden pre-activation within `margin` of 0: there the
+    ReLU subgradient flips with the last bit of the arithmetic (FP32 vs FP64), a
+    difference in which side of the kink is taken, not in the arithmetic."""
+    _, cache = oracle.train.forward(wl.latents, wl.shifts, wl.mlp.weights, wl.mlp.biases, uv)
+    keep = np.ones(len(uv), dtype=bool)
+    for z in cache["pre"][:-1]:
+        keep &= np.abs(z).min(axis=1) > margin
+    return uv[keep]
+
+
+def _oracle_grads(wl, uv, kind="mse"):
+    y, cache = oracle.train.forward(wl.latents, wl.shifts, wl.mlp.weights, wl.mlp.biases, uv)
+    loss, dy = oracle.train.loss_and_dy(y, oracle.train.target_sample(wl.target, uv), kind)
+    dW, db, dlat = oracle.train.backward(dy, cache, wl.latents, wl.shifts, wl.mlp.weights)
+    return y, loss, dW, db, dlat
+
+
+def _check_all_grads(model, dW, db, dlat):
+    gw, gb = model.grad_w.cpu().numpy(), model.grad_b.cpu().numpy()
+    for l, ((w0, w1), (b0, b1)) in enumerate(model.layer_slices()):
+        _check_grad(gw[w0:w1], dW[l], f"W{l}")
+        _check_grad(gb[b0:b1], db[l], f"b{l}")
+    for k in range(4):
+        _check_grad(model.latent_grads[k].cpu().numpy(), dlat[k], f"latent{k}")
+
+
+def _mid_workload(seed=77):
+    """Latents 128^2..16^2, target 256^2, batch 20000 (+ a ragged tile)."""
+    rng = synth.Rng(seed, 1)
+    sides = [128, 64, 32, 16]
+    lat = [rng.normal(s * s * 3, 0.1).reshape(s, s, 3).astype(np.float32) for s in sides]
+    mlp = synth.he_mlp(synth.Rng(seed, 2), [12, 64, 64, 9])
+    target = synth.sinusoid_target(synth.Rng(seed, 3), 256)
+    return synth.TrainWorkload("train-mid", sides, synth.SHIFTS, lat, mlp, target, 20000 + 37, seed)
+
+
+@pytest.mark.parametrize("which", ["reduced", "mid"])
+@pytest.mark.parametrize("kind", ["mse", "l1"])
+def test_forward_loss_and_gradients(nb, ctx, which, kind):
+    from paper_2506_06040_gb300.train import ContinuousModel
+    wl = synth.train_workload(full=False) if which == "reduced" else _mid_workload()
+    uv = kink_free(wl, wl.uv(0))
+    model = ContinuousModel.from_synth(wl)
+    uvd = torch.from_numpy(uv).cuda()
+    tgt = torch.from_numpy(wl.target).cuda()
+    y = model.forward(ctx, uvd)
+    ctx.sync()
+    y_ref, loss_ref, dW, db, dlat = _oracle_grads(wl, uv, kind)
+    assert np.abs(y.cpu().numpy() - y_ref).max() <= 1e-5
+    loss = model.train_step(ctx, uvd, tgt, loss=nb.LOSS_L1 if kind == "l1" else nb.LOSS_MSE)
+    ctx.sync()
+    assert abs(float(loss.item()) - loss_ref) <= REL * abs(loss_ref)
+    _check_all_grads(model, dW, db, dlat)
+
+
+def test_adam_updates_three_steps(nb, ctx):
+    from paper_2506_06040_gb300.train import ContinuousModel
+    wl = synth.train_workload(full=False)
+    model = ContinuousModel.from_synth(wl)
+    st = oracle.train.init_state(wl.latents, wl.mlp.weights, wl.mlp.biases)
+    tgt = torch.from_numpy(wl.target).cuda()
+    for step in range(3):
+        uv = kink_free(wl, wl.uv(step))
+        model.train_step(ctx, torch.from_numpy(uv).cuda(), tgt)
+        st = oracle.train.train_step(st, wl.shifts, wl.target, uv)
+    ctx.sync()
+    # parameters: Adam moves each by about lr per step; compare within lr * 1e-3
+    w = model.weights.cpu().numpy()
+    for l, ((w0, w1), _) in enumerate(model.layer_slices()):
+        assert np.abs(w[w0:w1] - st["weights"][l].ravel()).max() <= 1e-3 * 1e-3
+    for k in range(4):
+        assert np.abs(model.latents[k].cpu().numpy() - st["latents"][k]).max() <= 1e-2 * 1e-3
+        m = model.latent_m[k].cpu().numpy()
+        assert np.abs(m - st["m_latents"][k]).max() <= REL * np.abs(st["m_latents"][k]).max() + 1e-12
+
+
+def test_full_size_step(nb, ctx):
+    """The benchmark's configuration: latents 1024^2..128^2, target 2048^2 x 9,
+    batch 2^20.  MLP gradients and loss against the oracle on the whole batch;
+    latent gradients through the full FP64 backward."""
+    from paper_2506_06040_gb300.train import ContinuousModel
+    wl = synth.train_workload(full=True)
+    uv = kink_free(wl, wl.uv(0))
+    assert len(uv) > 0.95 * wl.batch
+    model = ContinuousModel.from_synth(wl)
+    loss = model.train_step(ctx, torch.from_numpy(uv).cuda(), torch.from_numpy(wl.target).cuda())
+    ctx.sync()
+    _, loss_ref, dW, db, dlat = _oracle_grads(wl, uv)
+    assert abs(float(loss.item()) - loss_ref) <= REL * abs(loss_ref)
+    _check_all_grads(model, dW, db, dlat)
+
+
+def test_autograd_function(nb, ctx):
+    from paper_2506_06040_gb300.train import ContinuousModel, NbtcDecodeFn
+    wl = synth.train_workload(full=False)
+    uv = kink_free(wl, wl.uv(1))
+    model = ContinuousModel.from_synth(wl)
+    lats = [l.clone().requires_grad_(True) for l in model.latents]
+    w = model.weights.clone().requires_grad_(True)
+    b = model.biases.clone().requires_grad_(True)
+    uvd = torch.from_numpy(uv).cuda()
+    y = NbtcDecodeFn.apply(ctx, model, uvd, *lats, w, b)
+    t = torch.from_numpy(oracle.train.target_sample(wl.target, uv)).cuda().float()
+    loss = ((y - t) ** 2).mean()
+    loss.backward()
+    _, loss_ref, dW, db, dlat = _oracle_grads(wl, uv)
+    assert abs(float(loss.item()) - loss_ref) <= REL * abs(loss_ref)
+    gw, gb = w.grad.cpu().numpy(), b.grad.cpu().numpy()
+    for l, ((w0, w1), (b0, b1)) in enumerate(model.layer_slices()):
+        _check_grad(gw[w0:w1], dW[l], f"W{l}")
+        _check_grad(gb[b0:b1], db[l], f"b{l}")
+    for k in range(4):
+        _check_grad(lats[k].grad.cpu().numpy(), dlat[k], f"latent{k}")
+
+
+def test_empty_batch_and_invalid(nb, ctx):
+    from paper_2506_06040_gb300.train import ContinuousModel
+    wl = synth.train_workload(full=False)
+    model = ContinuousModel.from_synth(wl)
+    y = model.forward(ctx, torch.empty((0, 2), device="cuda"))
+    assert y.shape == (0, 9)
+    with pytest.raises(nb.NbtcError):
+        model.train_step(ctx, torch.from_numpy(wl.uv(0)).cuda(), None)  # no target
+    ctx.sync()
