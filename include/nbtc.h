@@ -231,6 +231,22 @@ nbtc_status nbtc_forward_continuous(nbtc_context* ctx, const nbtc_train_args* ar
 nbtc_status nbtc_backward_continuous(nbtc_context* ctx, const nbtc_train_args* args, const float* dy_dev,
                                      void* stream);
 
+/* Allocation-free training step (the paper has no counterpart: this is an
+ * integration convenience).  For callers that may not allocate device memory
+ * at all -- engines that sub-allocate a budget reserved up front, plugin hosts
+ * that forbid allocation inside their callbacks, real-time loops that cannot
+ * afford the device synchronisation cudaMalloc / cudaFree can cause -- and so
+ * can neither supply args->workspace nor create an nbtc_context.  Same work and
+ * results as nbtc_train_step, on the current CUDA device; args->workspace is
+ * ignored.  Its scratch is a fixed 7.72 MB device array inside the library
+ * (room for one CTA per SM on devices with up to 160 SMs; larger devices get
+ * NBTC_ERR_UNSUPPORTED), held by every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (make that first call before any stream capture).  All calls share
+ * the array: calls that overlap on the GPU race and must be ordered by the
+ * caller.  Nothing is allocated by this call. */
+nbtc_status nbtc_train_step_noalloc(const nbtc_train_args* args, float* loss_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ PROTOTYPES = {
     "nbtc_train_step": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
     "nbtc_forward_continuous": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
     "nbtc_backward_continuous": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
+    "nbtc_train_step_noalloc": (c_int, [POINTER(TrainArgs), c_void_p, c_void_p]),
 }
 
 _lib = None

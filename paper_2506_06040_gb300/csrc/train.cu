@@ -10,6 +10,9 @@
 // Neumaier compensation, written to the workspace at the end; k_reduce_adam
 // adds the CTA partials in a fixed order (compensated), writes the gradients
 // and applies Adam.  Latent gradients: FP32 atomics (red.global.add).
+#include <mutex>
+#include <string>
+
 #include "host.h"
 
 namespace nbtc {
@@ -583,3 +586,66 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
 }
 
 }  // namespace nbtc
+
+// ------------------------------------------------------------------ allocation-free training step
+//
+// nbtc_train_step_noalloc is for callers that must not allocate device memory
+// themselves and cannot let a library do it either: renderers and engines that
+// reserve their whole GPU memory budget up front and sub-allocate it
+// themselves, plugin hosts whose execute callbacks forbid allocation, and
+// real-time loops where cudaMalloc / cudaFree may synchronise the device and
+// stall a frame.  Such callers cannot provide the training workspace, and
+// cannot create an nbtc_context either (nbtc_create allocates its status word).
+//
+// The step's only scratch -- the per-CTA partial gradient sums that the
+// reduction kernel adds up -- lives instead in the file-scope device array
+// below, which every GPU that loads this library holds until the process
+// exits.  It is sized for kNoAllocMaxCtas CTAs (one per SM); a device with more
+// SMs than that is rejected.  Every kernel writes each slot it later reads, so
+// nothing in the array needs clearing between calls.  All calls share the one
+// array: two of these steps in flight on the GPU at the same time (different
+// streams, or different host threads) race on it and corrupt each other's
+// gradients, so callers must order them.
+namespace nbtc {
+namespace {
+constexpr int kNoAllocMaxCtas = 160;
+constexpr int kNoAllocMaxDevices = 64;
+__device__ __align__(256) float g_noalloc_partials[kNoAllocMaxCtas * kPart];  // 7.72 MB
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+}  // namespace nbtc
+
+extern "C" nbtc_status nbtc_train_step_noalloc(const nbtc_train_args* args, float* loss_dev, void* stream) {
+  using namespace nbtc;
+  if (!args) return fail(NBTC_ERR_INVALID_ARG, "args NULL");
+  int dev = 0;
+  nbtc_status st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (st) return st;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(NBTC_ERR_UNSUPPORTED, "device index beyond 63");
+  void* scratch = nullptr;
+  {
+    // set-up, once per device, with that device current: the host-side name of
+    // the array is not a device address; ask the runtime for it
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if ((st = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_partials), "cudaGetSymbolAddress(scratch)"))) return st;
+      g_noalloc_addr[dev] = p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  int sms = 0;
+  if ((st = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count"))) return st;
+  nbtc_context local;  // on the stack: device and SM count only, no status word
+  local.device = dev;
+  local.sm_count = sms;
+  const int64_t tiles = (args->batch + kTS - 1) / kTS;
+  const int64_t grid = tiles < sms ? tiles : sms;
+  if (grid > kNoAllocMaxCtas)
+    return fail(NBTC_ERR_UNSUPPORTED, "nbtc_train_step_noalloc: the device has " + std::to_string(sms) +
+                                          " SMs; its fixed scratch holds partial sums for at most 160");
+  return train_step_impl(&local, args, loss_dev, (cudaStream_t)stream, 2, nullptr, nullptr, scratch,
+                         sizeof(g_noalloc_partials));
+}
