@@ -207,6 +207,31 @@ def run_forms(args, nb, ctx, stream, flush, peaks, sm_count) -> dict:
     return res
 
 
+def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
+    """One optimisation step on continuous latents (latents 1024^2..128^2, target
+    2048^2 x 9, batch 2^20 uniform uv, MLP 12-64-64-9, MSE, Adam): forward, loss,
+    backward into MLP and every latent texel, compensated reduction, Adam."""
+    import torch
+
+    from paper_2506_06040_gb300.train import ContinuousModel
+    wl = synth.train_workload(full=True)
+    model = ContinuousModel.from_synth(wl)
+    tgt = torch.from_numpy(wl.target).cuda()
+    uvs = [torch.from_numpy(wl.uv(i)).cuda() for i in range(4)]
+    it = iter(range(1 << 30))
+    t = _time_steps(lambda: model.train_step(ctx, uvs[next(it) % 4], tgt, stream=stream),
+                    max(3, args.steps // 2), args.warmup, flush, stream)
+    ms = statistics.mean(t)
+    flop = 32640 * wl.batch
+    peak = _fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    ctx.sync(stream)
+    return {"workload": wl.name, "steps_per_s": 1e3 / ms, "samples_per_s": wl.batch * 1e3 / ms, "ms_per_step": ms,
+            "kernels_per_step": 6,
+            "roofline": {"bound": "alu", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flop / (ms * 1e-3) / 1e12 / peak,
+                         "note": "whole step (forward, backward, reduction, Adam) against the FP32 FFMA peak"}}
+
+
 def run_ours(args) -> dict | None:
     import torch
 
@@ -306,6 +331,8 @@ def run_ours(args) -> dict | None:
     }
     if "forms" in args.parts:
         res["forms"] = run_forms(args, nb, ctx, stream, flush, peaks, sm_count)
+    if "train" in args.parts:
+        res["train"] = run_train(args, nb, ctx, stream, flush, sm_count, peaks)
     ctx.close()
     if world > 1:
         import torch.distributed as dist
@@ -343,7 +370,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--parts", default="main,forms", help="comma list: main (always), forms")
+    ap.add_argument("--parts", default="main,forms,train", help="comma list: main (always), forms, train")
     ap.add_argument("--form-side", type=int, default=4096, help="output side of the precision-form workload")
     ap.add_argument("--side", type=int, default=4096, help="output side (4096 = the benchmark workload; "
                     "smaller sides are for profiling captures)")

@@ -231,6 +231,73 @@ nbtc_status nbtc_forward_continuous(nbtc_context* ctx, const nbtc_train_args* ar
 nbtc_status nbtc_backward_continuous(nbtc_context* ctx, const nbtc_train_args* args, const float* dy_dev,
                                      void* stream);
 
+/* ------------------------------------------------------------------ batching
+ *
+ * Many materials, each with its own BC1 pyramid (with mips) and its own MLP,
+ * decoded in one persistent launch (Sec. 4: the G-buffer pass runs every
+ * neural material of a frame; cooperative vectors need one matrix per
+ * workgroup, so pixels are grouped per MLP).  A plan owns the device-side
+ * material table, the packed FP16 MLPs, the work lists and two CUDA graphs.
+ *
+ * Full decode: every material with `out` set is decoded on its texel-centre
+ * grid (mip 0, the material's address mode) into `out` (FP16, out_w % 128 == 0).
+ *
+ * Frame (Algorithm 1): each pixel carries a material id (-1: none), uv and lod
+ * = log2(uv footprint of the pixel) + mip bias.  Pass A classifies 128-pixel
+ * tiles (tile_w x tile_h) as uniform (one material, more than half the pixels
+ * valid) or mixed; an exclusive scan gives each material its slot offsets; pass
+ * B packs the valid pixels of mixed tiles into 128-slot tiles of one material.
+ * Each pixel is then decoded with per-level lod_k = lod + log2(W_k) (clamped to
+ * the level's mips, trilinear) and its material's MLP; the C FP16 channels go
+ * to out[pixel].  Pixels with id -1 are left untouched. */
+typedef struct {
+  nbtc_latents latents;   /* 4 levels (with mips for the frame) */
+  nbtc_mlp mlp;           /* FP32 [12, 64, .., 64, C]; the same depth and C for every material */
+  int32_t out_w, out_h;   /* full-decode grid (0 = not decoded in full) */
+  void* out;              /* device FP16 [out_h][out_w][C] */
+} nbtc_batch_material;
+
+typedef struct {
+  int32_t width, height;  /* pixels */
+  const int32_t* mat_id;  /* [height][width] material index or -1 */
+  const float* uv;        /* [height][width][2] */
+  const float* lod;       /* [height][width] */
+  void* out;              /* FP16 [height][width][C] */
+} nbtc_frame;
+
+typedef struct nbtc_batch nbtc_batch;
+
+/* What a plan chose and counted (after nbtc_batch_create / the last render). */
+typedef struct {
+  int32_t warpgroups;      /* tile groups per CTA of the decode kernel */
+  int32_t chunk_tiles;     /* tiles per work chunk */
+  int32_t tile_w, tile_h;  /* frame classification tile */
+  int64_t decode_tiles;    /* 128-texel tiles of the full decode */
+  int64_t frame_uniform_tiles, frame_mixed_tiles, frame_packed_tiles;  /* of the last render */
+  float tuned_decode_ms, tuned_render_ms;  /* autotuner's best times (0 = not tuned) */
+} nbtc_batch_info;
+
+#define NBTC_BATCH_AUTOTUNE 1  /* flags: time the candidate configurations at creation */
+
+/* Builds a plan (allocates its device buffers, packs the MLPs in FP16, builds
+ * the work lists, autotunes if asked, captures the graphs).  `mats` is a host
+ * array of `count` materials (<= 1024); `frame` may be NULL.  Device pointers in
+ * `mats` and `frame` must stay valid while the plan is used. */
+nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats, int32_t count,
+                              const nbtc_frame* frame, int32_t flags, nbtc_batch** plan, void* stream);
+
+/* Full decode of every material (one graph launch: counter reset + one
+ * persistent kernel). */
+nbtc_status nbtc_decode_batched(nbtc_context* ctx, nbtc_batch* plan, void* stream);
+
+/* Frame: classify, scan, bin, decode (one graph launch). */
+nbtc_status nbtc_render_frame(nbtc_context* ctx, nbtc_batch* plan, void* stream);
+
+nbtc_status nbtc_batch_info_get(nbtc_batch* plan, nbtc_batch_info* info);
+
+/* Frees the plan (synchronises its device first). */
+nbtc_status nbtc_batch_destroy(nbtc_batch* plan);
+
 /* Allocation-free training step (the paper has no counterpart: this is an
  * integration convenience).  For callers that may not allocate device memory
  * at all -- engines that sub-allocate a budget reserved up front, plugin hosts

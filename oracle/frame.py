@@ -90,3 +90,51 @@ def level_mips_rgb(level) -> list:
         out.append(bc1.decode_level(blocks, w, h).astype(np.float64) / 255.0)
         w, h = max(4, w // 2), max(4, h // 2)
     return out
+
+
+def _bilinear_bc1(level_blocks, w, h, u, v, shift, address):
+    """Bilinear sample of one BC1 mip (w x h) at (u, v), fetching only the four
+    texels each sample needs (same filter as sample.bilinear)."""
+    x = np.asarray(u, dtype=np.float64) * w - 0.5 + shift
+    y = np.asarray(v, dtype=np.float64) * h - 0.5 + shift
+    x0, y0 = np.floor(x), np.floor(y)
+    fx, fy = (x - x0)[..., None], (y - y0)[..., None]
+    x0, y0 = x0.astype(np.int64), y0.astype(np.int64)
+    if address == "wrap":
+        xa, xb, ya, yb = np.mod(x0, w), np.mod(x0 + 1, w), np.mod(y0, h), np.mod(y0 + 1, h)
+    else:
+        xa, xb = np.clip(x0, 0, w - 1), np.clip(x0 + 1, 0, w - 1)
+        ya, yb = np.clip(y0, 0, h - 1), np.clip(y0 + 1, 0, h - 1)
+    t = lambda xx, yy: bc1.texel_rgb8(level_blocks, w, xx, yy).astype(np.float64) / 255.0
+    return ((1 - fx) * (1 - fy) * t(xa, ya) + fx * (1 - fy) * t(xb, ya)
+            + (1 - fx) * fy * t(xa, yb) + fx * fy * t(xb, yb))
+
+
+def decode_pixels_direct(material, uv: np.ndarray, lod: np.ndarray, precision: str = "fp16") -> np.ndarray:
+    """decode_pixels without decoding whole mips: each tap's BC1 texel is
+    decoded on demand (for spot checks of large frames)."""
+    u, v = uv[:, 0].astype(np.float64), uv[:, 1].astype(np.float64)
+    feats = []
+    for lv in material.levels:
+        mips = lv.num_mips
+        lam = np.clip(lod.astype(np.float64) + np.log2(float(lv.width)), 0.0, mips - 1)
+        m0 = np.floor(lam).astype(np.int64)
+        m1 = np.minimum(m0 + 1, mips - 1)
+        t = (lam - m0)[:, None]
+        acc = np.zeros((len(u), 3))
+        w, h = lv.width, lv.height
+        for m in range(mips):
+            sel0, sel1 = m0 == m, m1 == m
+            sel = sel0 | sel1
+            if np.any(sel):
+                smp = _bilinear_bc1(lv.blocks[m], w, h, u[sel], v[sel], lv.shift, material.address)
+                wt = np.where(sel0[sel][:, None], 1 - t[sel], 0.0) + np.where(sel1[sel][:, None], t[sel], 0.0)
+                acc[sel] += wt * smp
+            w, h = max(4, w // 2), max(4, h // 2)
+        feats.append(acc)
+    x = np.concatenate(feats, axis=-1)
+    mlp = material.mlp
+    if precision == "fp16":
+        return emulate.forward_fp16(x, mlp.weights, mlp.biases)
+    from . import mlp as mlp_mod
+    return mlp_mod.forward(x, mlp.weights, mlp.biases)

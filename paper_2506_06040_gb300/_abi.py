@@ -45,6 +45,24 @@ class TrainArgs(ctypes.Structure):
                 ("workspace_bytes", c_size_t)]
 
 
+class BatchMaterial(ctypes.Structure):
+    _fields_ = [("latents", Latents), ("mlp", Mlp), ("out_w", c_int32), ("out_h", c_int32), ("out", c_void_p)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("mat_id", c_void_p), ("uv", c_void_p),
+                ("lod", c_void_p), ("out", c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("warpgroups", c_int32), ("chunk_tiles", c_int32), ("tile_w", c_int32), ("tile_h", c_int32),
+                ("decode_tiles", c_int64), ("frame_uniform_tiles", c_int64), ("frame_mixed_tiles", c_int64),
+                ("frame_packed_tiles", c_int64), ("tuned_decode_ms", c_float), ("tuned_render_ms", c_float)]
+
+
+BATCH_AUTOTUNE = 1
+
+
 # name -> (restype, argtypes)
 PROTOTYPES = {
     "nbtc_create": (c_int, [c_int, POINTER(c_void_p)]),
@@ -65,6 +83,12 @@ PROTOTYPES = {
     "nbtc_forward_continuous": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
     "nbtc_backward_continuous": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
     "nbtc_train_step_noalloc": (c_int, [POINTER(TrainArgs), c_void_p, c_void_p]),
+    "nbtc_batch_create": (c_int, [c_void_p, POINTER(BatchMaterial), c_int32, POINTER(Frame), c_int32,
+                                  POINTER(c_void_p), c_void_p]),
+    "nbtc_decode_batched": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "nbtc_render_frame": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "nbtc_batch_info_get": (c_int, [c_void_p, POINTER(BatchInfo)]),
+    "nbtc_batch_destroy": (c_int, [c_void_p]),
 }
 
 _lib = None

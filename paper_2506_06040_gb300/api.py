@@ -154,3 +154,60 @@ def decode(ctx: Context, mat: Material, precision: int = _abi.FP32, packed=None,
     check(ctx.lib.nbtc_decode(ctx.handle, byref(lat), byref(m), precision, _ptr(packed), _ptr(uv), n, gw, gh,
                               _ptr(out), _stream(stream)))
     return out
+
+
+class Batch:
+    """A batched-decode plan: many materials (each with its own BC1 pyramid and
+    FP32 MLP, decoded in FP16 on tensor cores) decoded in one persistent
+    graph-captured launch, and optionally a frame rendered through the tile
+    classification / binning pipeline.
+
+    materials: list of Material; outs: list of (tensor FP16 [h*w, C], w, h) or
+    None per material; frame: dict(mat_id int32 [h, w], uv FP32 [h, w, 2],
+    lod FP32 [h, w], out FP16 [h, w, C]) or None."""
+
+    def __init__(self, ctx: Context, materials, outs=None, frame=None, autotune=True, stream=None):
+        self.ctx = ctx
+        self.materials = list(materials)
+        self.outs = list(outs) if outs is not None else [None] * len(self.materials)
+        self.frame = frame
+        arr = (_abi.BatchMaterial * len(self.materials))()
+        for i, (m, o) in enumerate(zip(self.materials, self.outs)):
+            arr[i].latents = m.latents_struct()
+            arr[i].mlp = m.mlp_struct()
+            if o is not None:
+                t, w, h = o
+                arr[i].out, arr[i].out_w, arr[i].out_h = t.data_ptr(), w, h
+        fr = None
+        if frame is not None:
+            fr = _abi.Frame()
+            fr.height, fr.width = int(frame["mat_id"].shape[0]), int(frame["mat_id"].shape[1])
+            fr.mat_id, fr.uv, fr.lod, fr.out = (frame["mat_id"].data_ptr(), frame["uv"].data_ptr(),
+                                                frame["lod"].data_ptr(), frame["out"].data_ptr())
+        h = c_void_p()
+        flags = _abi.BATCH_AUTOTUNE if autotune else 0
+        check(ctx.lib.nbtc_batch_create(ctx.handle, arr, len(self.materials), byref(fr) if fr is not None else None,
+                                        flags, byref(h), _stream(stream)))
+        self.handle = h
+
+    def decode(self, stream=None):
+        check(self.ctx.lib.nbtc_decode_batched(self.ctx.handle, self.handle, _stream(stream)))
+
+    def render(self, stream=None):
+        check(self.ctx.lib.nbtc_render_frame(self.ctx.handle, self.handle, _stream(stream)))
+
+    def info(self) -> dict:
+        i = _abi.BatchInfo()
+        check(self.ctx.lib.nbtc_batch_info_get(self.handle, byref(i)))
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.nbtc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -84,6 +84,9 @@ __device__ __forceinline__ uint32_t fetch_texel(const LevelView& L, int x, int y
 // are clamped to [0, n-1] or wrapped modulo n.
 __device__ __forceinline__ void axis_taps(float u, int n, float shift, bool wrap, int& i0, int& i1,
                                           float& f) {
+  // wrap: drop whole periods of u first (u - floor(u) is exact), so the texel
+  // coordinate keeps its fraction even for tiled uv far from [0, 1)
+  if (wrap) u -= floorf(u);
   float t = fmaf(u, (float)n, shift - 0.5f);
   if (wrap) {
     t -= (float)n * floorf(t / (float)n);  // into [0, n)

@@ -53,6 +53,15 @@ nbtc_status make_level_views(const nbtc_latents* lat, int mip, LevelView* views)
     if (L.num_mips < 1 || L.num_mips > NBTC_MAX_MIPS)
       return fail(NBTC_ERR_INVALID_ARG, "num_mips must be 1..16");
     if (mip < 0 || mip >= L.num_mips) return fail(NBTC_ERR_INVALID_ARG, "mip out of range");
+    {  // every mip must tile into whole 4x4 blocks: mip m is max(4, size >> m)
+      int w = L.width, h = L.height;
+      for (int m = 1; m < L.num_mips; ++m) {
+        if ((w / 2 >= 4 && (w / 2) % 4) || (h / 2 >= 4 && (h / 2) % 4) || (w % 2 && w > 4) || (h % 2 && h > 4))
+          return fail(NBTC_ERR_INVALID_ARG, "a mip is not a whole number of 4x4 blocks");
+        w = w / 2 < 4 ? 4 : w / 2;
+        h = h / 2 < 4 ? 4 : h / 2;
+      }
+    }
     if (!(L.shift > -64.f && L.shift < 64.f)) return fail(NBTC_ERR_INVALID_ARG, "shift out of range");
     size_t off = 0;
     int w = L.width, h = L.height;

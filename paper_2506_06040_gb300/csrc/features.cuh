@@ -174,6 +174,47 @@ __device__ __forceinline__ void footprint_features(const DecodeArgs& a, int64_t 
   blend_columns<NT>(a, P, tid, colbuf, feat);
 }
 
+// Per-material description used by the batched and frame decodes: the level
+// views of mip 0 (in `d`) plus every level's mip chain for trilinear sampling.
+struct MatDev {
+  DecodeArgs d;          // mip-0 views, wrap flag, output grid and buffer of the full decode
+  const void* packed;    // FP16 packed MLP
+  int nout;
+  int tiles_per_row;     // full decode: grid_w / 128
+  int64_t tiles;         // full decode: tiles of the grid
+  int mips[4];
+  float log2w[4];        // log2 of each level's mip-0 width
+  int mip_off[4][16];    // block offset of mip m of level k
+};
+
+__device__ __forceinline__ LevelView mip_view(const MatDev& M, int k, int m) {
+  LevelView v = M.d.lv[k];
+  v.blocks = v.blocks + M.mip_off[k][m];
+  v.w = max(4, v.w >> m);
+  v.h = max(4, v.h >> m);
+  v.wb = v.w / 4;
+  return v;
+}
+
+// Features of one pixel of the frame: per level, lod_k = lod + log2(W_k)
+// clamped to the mip range, trilinear (bilinear in mips floor(lod_k) and the
+// next, blended by its fraction), the material's address mode.
+__device__ __forceinline__ void trilinear_features(const MatDev& M, float u, float v, float lod, float (&feat)[12]) {
+  const bool wrap = M.d.wrap;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float lam = fminf(fmaxf(lod + M.log2w[k], 0.f), (float)(M.mips[k] - 1));
+    const int m0 = (int)floorf(lam);
+    const int m1 = min(m0 + 1, M.mips[k] - 1);
+    const float t = lam - (float)m0;
+    const float3 c0 = sample_bilinear(mip_view(M, k, m0), u, v, wrap);
+    const float3 c1 = sample_bilinear(mip_view(M, k, m1), u, v, wrap);
+    feat[3 * k + 0] = fmaf(t, c1.x - c0.x, c0.x);
+    feat[3 * k + 1] = fmaf(t, c1.y - c0.y, c0.y);
+    feat[3 * k + 2] = fmaf(t, c1.z - c0.z, c0.z);
+  }
+}
+
 // Features of one texel sampled on its own (any uv).
 __device__ __forceinline__ void direct_features(const DecodeArgs& a, int64_t t, float (&feat)[12]) {
   const float2 uv = texel_uv(a, t);

@@ -1,0 +1,112 @@
+// Types shared by the tensor-core decode kernel and its launchers (single
+// material, batched materials, frame).
+#pragma once
+
+#include "features.cuh"
+#include "host.h"
+
+namespace nbtc {
+
+constexpr int kTile = 128;           // texels per tile = MMA M
+constexpr int kHid = 64;             // hidden width of the tensor-core forms
+constexpr int kOutPad = 16;          // output layer N (channels padded)
+constexpr int kMaxOut = 16;
+
+// Byte layout of a packed MLP (identical in global memory and shared memory).
+// FP16: every layer's bias enters the MMA as an FP16 operand -- layer 1 through
+// K column 12 of W1 (A0 carries a 1 there), later layers through a small
+// [N x 16] bias tile multiplied by a tile of ones.  FP8: the FP32 bias and the
+// per-layer scale are applied in the epilogue.
+struct TcLayout {
+  int nhid;   // hidden layers (1..3)
+  bool fp8;
+  __host__ __device__ int esz() const { return fp8 ? 1 : 2; }
+  __host__ __device__ int wh_bytes() const { return kHid * kHid * esz(); }   // 64 x 64
+  __host__ __device__ int bth_bytes() const { return fp8 ? 0 : kHid * 16 * 2; }   // 64 x 16 bias tile
+  __host__ __device__ int wo_bytes() const { return kOutPad * kHid * esz(); }   // 16 x 64
+  __host__ __device__ int bto_bytes() const { return fp8 ? 0 : kOutPad * 16 * 2; }  // 16 x 16 bias tile
+  __host__ __device__ int off_w1() const { return 0; }                                // 64 x K1: 2048 B
+  __host__ __device__ int off_wh(int l) const { return 2048 + l * (wh_bytes() + bth_bytes()); }  // l < nhid-1
+  __host__ __device__ int off_bth(int l) const { return off_wh(l) + wh_bytes(); }
+  __host__ __device__ int off_wo() const { return off_wh(nhid - 1); }
+  __host__ __device__ int off_bto() const { return off_wo() + wo_bytes(); }
+  __host__ __device__ int off_bias() const { return off_bto() + bto_bytes(); }    // nhid*64 + 16 floats
+  __host__ __device__ int off_alpha() const { return off_bias() + (nhid * kHid + kOutPad) * 4; }  // 8 floats
+  __host__ __device__ int bytes() const { return (off_alpha() + 8 * 4 + 15) & ~15; }
+};
+
+// Offset of element (row, k) in a K-major operand tile.
+//  no swizzle, 16-byte core matrices of 8 rows: LBO = 128 B (next K chunk), SBO = 256 B (next 8 rows)
+__host__ __device__ inline uint32_t off_interleave(int row, int kbyte) {
+  return (uint32_t)((row >> 3) * 256 + (kbyte >> 4) * 128 + (row & 7) * 16 + (kbyte & 15));
+}
+//  128-byte swizzle, 128-byte rows (64 f16): atom 8 rows x 128 B, SBO = 1024 B
+__host__ __device__ inline uint32_t off_sw128(int row, int kbyte) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((kbyte >> 4) ^ (row & 7)) & 7) << 4) + (kbyte & 15));
+}
+//  64-byte swizzle, 64-byte rows (64 e4m3): atom 8 rows x 64 B, SBO = 512 B
+__host__ __device__ inline uint32_t off_sw64(int row, int kbyte) {
+  return (uint32_t)((row >> 3) * 512 + (row & 7) * 64 + ((((kbyte >> 4) ^ ((row & 7) >> 1)) & 3) << 4) +
+                    (kbyte & 15));
+}
+
+// A run of tiles of one material: full-decode row tiles (numbered column-major
+// within the material), or frame tiles -- uniform (a list of 128-pixel screen
+// tiles) or packed (128-slot lists of pixel indices).
+enum ChunkKind { kChunkGrid = 0, kChunkUniform = 1, kChunkPacked = 2 };
+struct WorkChunk {
+  int mat;
+  int kind;
+  int64_t first;
+  int count;
+  int pad;
+};
+
+enum TcMode { kModeSingle = 0, kModeBatch = 1 };
+
+struct TcArgs {
+  DecodeArgs d;
+  const void* packed;
+  int nout;
+  int footprint;       // 1: row-footprint feature stage
+  int tiles_per_row;   // footprint mode: grid_w / 128
+  int64_t tiles;
+  int64_t per_cta;     // tiles per CTA (contiguous range)
+  long long budget;    // polls per bounded wait
+  // batched materials / frame
+  int mode;
+  const MatDev* mats;
+  const WorkChunk* chunks;
+  const int* nchunks_dev;  // chunk count, read on the device
+  int* chunk_counter;      // next chunk to take (zeroed before the launch)
+  const int* ulist;        // frame: uniform screen tiles
+  const int* plist;        // frame: packed pixel indices (128 per tile, -1 = none)
+  const int* fmat;         // frame: per-pixel material id
+  const float* fuv;        // frame: per-pixel uv
+  const float* flod;       // frame: per-pixel lod (log2 of the uv footprint + bias)
+  uint16_t* fout;          // frame: per-pixel output (nout FP16)
+  int frame_w, tile_w, tile_h, tiles_x;
+};
+
+// Per-CTA view of the chunk being decoded (in shared memory).
+struct TcWork {
+  MatDev m;
+  WorkChunk c;
+  int valid;
+  int reload;
+};
+
+constexpr int kMmaWarps = 4;       // one MMA-issuing warp per SM sub-partition
+
+
+
+constexpr int kSlots = 2;          // tile slots per warpgroup (ping-pong)
+constexpr int kStageBytes = 1024;  // per-warp output staging (32 texels x <= 16 halves)
+
+
+struct TcArgs;
+// Launches the decode kernel (any mode) with W warpgroups on `grid` CTAs.
+nbtc_status launch_tc_args(nbtc_context* ctx, const struct TcArgs& p, int nhid, bool fp8, int W, int grid,
+                           cudaStream_t s);
+
+}  // namespace nbtc

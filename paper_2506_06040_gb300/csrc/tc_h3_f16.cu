@@ -1,0 +1,10 @@
+// Instantiation unit of the tensor-core decode kernel: 3 hidden layer(s), FP16 operands.
+#include "tc_kernel.cuh"
+
+namespace nbtc {
+
+nbtc_status launch_tc_h3_f16(const TcArgs& p, int W, int grid, cudaStream_t s) {
+  return W == 3 ? launch_tc_w<3, false, 3>(p, grid, s) : launch_tc_w<3, false, 4>(p, grid, s);
+}
+
+}  // namespace nbtc

@@ -1,0 +1,462 @@
+// The tensor-core decode kernel (template; instantiated in tc_h*_*.cu).
+//
+// FP16 or FP8 E4M3 operands, FP32 accumulation in TMEM, FP16 output: the
+// GB300 counterpart of the paper's cooperative-vector MLP (Sec. 4, "Neural
+// inference in G-Buffer pass"); each layer of a 128-texel tile is one chain of
+// tcgen05.mma with M = 128 texels, N = layer width, weights resident in shared
+// memory.
+//
+// Persistent, warp-specialised CTA (one per SM): W warpgroups of 128 threads
+// (one thread per tile row) compute features and run the epilogues, and
+// kMmaWarps warps issue the MMAs.  Each warpgroup owns two tile slots (TMEM
+// columns + A buffers) and alternates between them, so one slot's SIMT work
+// overlaps the other slot's MMAs.  The CTA walks "chunks" -- runs of tiles of
+// one material -- and reloads the packed MLP only when the material changes.
+#pragma once
+
+#include <cstring>
+
+#include "features.cuh"
+#include "host.h"
+#include "sm100.cuh"
+#include "tc.cuh"
+
+namespace nbtc {
+
+using namespace sm100;
+
+// Tile numbering.  Each CTA owns a contiguous range of tile numbers; in
+// row-footprint mode consecutive numbers run down a column of 128-texel tiles
+// (number -> row = T % H, column block = T / H), so the tiles a CTA decodes at
+// the same time sit on neighbouring rows and share latent blocks in L1.
+// Returns the first output texel of tile T.
+__device__ __forceinline__ int64_t tile_first_texel(const DecodeArgs& d, bool footprint, int64_t T) {
+  if (!footprint) return T * 128;
+  const uint32_t t = (uint32_t)T, h = (uint32_t)d.grid_h;
+  const uint32_t col = t / h, row = t - col * h;
+  return (int64_t)row * d.grid_w + (int64_t)col * 128;
+}
+
+// Frame pixel decoded by row `gt` of tile `T` of chunk `c` (-1: none).  A
+// uniform tile may hold pixels without a material: those are not decoded.
+__device__ __forceinline__ int64_t frame_pixel(const TcArgs& p, const WorkChunk& c, int64_t T, int gt) {
+  if (c.kind == kChunkUniform) {
+    const int ft = __ldg(p.ulist + c.first + T);
+    const int ty = ft / p.tiles_x, tx = ft - ty * p.tiles_x;
+    const int r = gt / p.tile_w;
+    const int64_t px = (int64_t)(ty * p.tile_h + r) * p.frame_w + tx * p.tile_w + (gt - r * p.tile_w);
+    return __ldg(p.fmat + px) == c.mat ? px : -1;
+  }
+  return __ldg(p.plist + (c.first + T) * 128 + gt);
+}
+
+// Shared-memory plan.  Per slot: A0 (128 x K1 operand) and Ah (128 x 64
+// operand, also the feature stage's column buffer while no MMA reads it).
+struct TcSmem {
+  int image;       // packed MLP (rounded to 1 KB)
+  int ones;        // 128 x 16 FP16 tile of ones in column 0
+  int slots;       // first slot
+  int slot;        // bytes per slot
+  int a0, ah;      // offsets inside a slot
+  int stage;       // per-warp output staging
+  int bars;        // A-ready[NS], D-ready[NS], weight barrier
+  int tslot;       // TMEM address slot
+  int work;        // TcWork
+  int total;
+};
+
+__host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W) {
+  TcSmem s;
+  const int NS = W * kSlots;
+  s.image = (L.bytes() + 1023) & ~1023;
+  s.ones = s.image;
+  s.slots = s.ones + 4096;
+  s.a0 = 0;
+  s.ah = 4096;
+  s.slot = 4096 + 16384;
+  s.stage = s.slots + NS * s.slot;
+  s.bars = s.stage + W * 4 * kStageBytes;
+  s.tslot = s.bars + (2 * NS + 1) * 8;
+  s.work = (s.tslot + 16 + 15) & ~15;
+  s.total = s.work + (int)((sizeof(TcWork) + 15) & ~(size_t)15) + 1024 /* alignment slack */;
+  return s;
+}
+
+// Warp-specialised persistent kernel: W warpgroups (4 warps, one thread per
+// tile row) compute features and epilogues; warp 4W issues every MMA.  Each
+// warpgroup owns two tile slots (TMEM columns + A buffers) and alternates
+// between them, so one slot's epilogue runs while the other slot's MMAs run.
+// Slot q walks tiles q + NS * (blockIdx.x + gridDim.x * i).
+//
+// Hand-offs (all mbarriers, all waits bounded):
+//   A-ready[q]  (128 arrivals): slot q's A operand for its next layer is in smem
+//   D-ready[q]  (tcgen05.commit): that layer's accumulator is in TMEM
+// After a timeout a thread stops waiting but keeps its schedule (every
+// barrier and arrival still happens), so the kernel always terminates.
+template <int NHID, bool FP8, int W>
+__global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArgs p) {
+  constexpr TcLayout L{NHID, FP8};
+  constexpr int NS = W * kSlots;
+  constexpr uint32_t kTmemCols = NS * kHid <= 256 ? 256 : 512;
+  static_assert(NS * kHid <= 512, "TMEM holds at most 512 columns");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const TcSmem S = tc_smem(L, W);
+  const uint32_t sbase = smem_u32(smem);
+  const int tid = threadIdx.x;
+  const int warp = tid / 32, lane = tid % 32;
+  const uint32_t abar0 = sbase + S.bars, dbar0 = abar0 + NS * 8, wbar = dbar0 + NS * 8;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S.tslot);
+  TcWork& work = *reinterpret_cast<TcWork*>(smem + S.work);
+  int* status = p.d.status;
+
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(abar0 + q * 8, kTile);
+      mbar_init(dbar0 + q * 8, 1);
+    }
+    mbar_init(wbar, 1);
+    fence_mbar_init();
+    work.m.packed = nullptr;
+    work.c.mat = -1;
+  }
+  if (!FP8 && tid < kTile) {  // ones tile: column 0 = 1.0 (FP16), rest 0
+    sts128(sbase + S.ones + off_interleave(tid, 0), 0x3C00u, 0u, 0u, 0u);
+    sts128(sbase + S.ones + off_interleave(tid, 16), 0u, 0u, 0u, 0u);
+    fence_proxy_async_smem();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  bool failed = false;
+  uint32_t wph = 0;  // phase of the weight barrier
+
+  // slot state that lives across chunks (mbarrier phases)
+  uint32_t aph[kMmaWarps > 0 ? (NS + kMmaWarps - 1) / kMmaWarps : 1] = {};
+  uint32_t dph[kSlots] = {};
+  bool first_chunk = true;
+
+  for (;;) {
+    // ---- take the next chunk (thread 0), load its material's MLP if it changed
+    if (tid == 0) {
+      int valid = 0, reload = 0;
+      if (p.mode == kModeSingle) {
+        if (first_chunk) {
+          const int64_t b = (int64_t)blockIdx.x * p.per_cta;
+          const int64_t e = b + p.per_cta < p.tiles ? b + p.per_cta : p.tiles;
+          work.m.d = p.d;
+          work.m.packed = p.packed;
+          work.m.nout = p.nout;
+          work.c.mat = 0;
+          work.c.kind = kChunkGrid;
+          work.c.first = b;
+          work.c.count = (int)(e > b ? e - b : 0);
+          valid = e > b;
+          reload = 1;
+        }
+      } else {
+        const int c = atomicAdd(p.chunk_counter, 1);
+        if (c < *p.nchunks_dev) {
+          const WorkChunk ch = p.chunks[c];
+          reload = ch.mat != work.c.mat;
+          if (reload) work.m = p.mats[ch.mat];
+          work.c = ch;
+          valid = 1;
+        }
+      }
+      if (valid && reload) {
+        mbar_expect_tx(wbar, (uint32_t)L.bytes());
+        bulk_g2s(sbase, work.m.packed, (uint32_t)L.bytes(), wbar);
+      }
+      work.valid = valid;
+      work.reload = reload;
+    }
+    __syncthreads();
+    first_chunk = false;
+    if (!work.valid) break;
+    if (work.reload) {
+      if (!failed) failed = !mbar_wait_bounded(wbar, wph, p.budget);
+      wph ^= 1u;
+    }
+    failed = __syncthreads_or(failed);
+    const bool grid_chunk = work.c.kind == kChunkGrid;
+    const bool footprint = p.mode == kModeSingle ? p.footprint != 0 : grid_chunk;
+    const int64_t range_end = work.c.count;   // tiles are numbered 0 .. count-1 inside the chunk
+
+    if (warp >= 4 * W) {
+      // ---------------------------------------------------------- MMA warps
+      // MMA warp m issues for slots q = m, m + kMmaWarps, ...  Descriptors are
+      // built once; per MMA only the 32-bit low word advances along K.
+      const int m = warp - 4 * W;
+      if (lane == 0 && m < NS) {
+        constexpr int NQ = (NS + kMmaWarps - 1) / kMmaWarps;
+        constexpr uint32_t ID_HID = idesc(0, kTile, kHid);
+        constexpr uint32_t ID_OUT = idesc(0, kTile, kOutPad);
+        // high words: SBO, version, swizzle; low words: start address, LBO
+        const uint32_t hi_int = (uint32_t)(smem_desc(0, 128, 256, kSwzNone) >> 32);
+        const uint32_t hi_w = FP8 ? (uint32_t)(smem_desc(0, 16, 512, kSwz64) >> 32)
+                                  : (uint32_t)(smem_desc(0, 16, 1024, kSwz128) >> 32);
+        auto lo = [](uint32_t addr, uint32_t lbo) { return (uint32_t)smem_desc(addr, lbo, 0, 0); };
+        const uint32_t lo_w1 = lo(sbase + L.off_w1(), 128);
+        const uint32_t lo_ones = lo(sbase + S.ones, 128);
+        int64_t next[NQ];
+        int stage[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+          next[i] = m + i * kMmaWarps;
+          stage[i] = 0;
+        }
+        long long idle = 0;
+        for (;;) {
+          bool any = false, progressed = false;
+#pragma unroll
+          for (int i = 0; i < NQ; ++i) {
+            const int q = m + i * kMmaWarps;
+            if (q >= NS || next[i] >= range_end) continue;
+            any = true;
+            if (!failed && !mbar_test_wait(abar0 + q * 8, aph[i])) continue;
+            aph[i] ^= 1u;
+            progressed = true;
+            tc_fence_after();
+            const uint32_t d = tmem_base + (uint32_t)(q * kHid);
+            const uint32_t slot = sbase + S.slots + q * S.slot;
+            const int l = stage[i];
+            if (l == 0) {
+              const uint64_t ad = ((uint64_t)hi_int << 32) | lo(slot + S.a0, 128);
+              const uint64_t bd = ((uint64_t)hi_int << 32) | lo_w1;
+              if constexpr (FP8) mma_f8(d, ad, bd, ID_HID, 0);
+              else mma_f16(d, ad, bd, ID_HID, 0);
+            } else {
+              const bool last = l == NHID;
+              const uint32_t id = last ? ID_OUT : ID_HID;
+              const uint32_t lo_a = lo(slot + S.ah, 16);
+              const uint32_t lo_b = lo(sbase + (last ? L.off_wo() : L.off_wh(l - 1)), 16);
+              if constexpr (FP8) {
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk)
+                  mma_f8(d, ((uint64_t)hi_w << 32) | (lo_a + 2 * kk), ((uint64_t)hi_w << 32) | (lo_b + 2 * kk), id,
+                         kk > 0);
+              } else {
+                const uint32_t lo_bt = lo(sbase + (last ? L.off_bto() : L.off_bth(l - 1)), 128);
+                mma_f16(d, ((uint64_t)hi_int << 32) | lo_ones, ((uint64_t)hi_int << 32) | lo_bt, id, 0);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                  mma_f16(d, ((uint64_t)hi_w << 32) | (lo_a + 2 * kk), ((uint64_t)hi_w << 32) | (lo_b + 2 * kk), id,
+                          1);
+              }
+            }
+            mma_commit(dbar0 + q * 8);
+            if (++stage[i] > NHID) {
+              stage[i] = 0;
+              next[i] += NS;
+            }
+          }
+          if (!any) break;
+          if (progressed) {
+            idle = 0;
+          } else if (++idle > p.budget) {
+            failed = true;  // stop waiting; finish the schedule without waits
+            record_status(status, NBTC_ERR_TIMEOUT);
+          }
+        }
+      }
+      __syncwarp();
+    } else {
+      // ---------------------------------------------------------- warpgroups
+      const int wg = warp / 4, wq = warp & 3;
+      const int gt = tid % kTile;
+      const int bar_id = 1 + wg;
+      const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
+      unsigned char* stage_w = smem + S.stage + warp * kStageBytes;
+      const float* bias = reinterpret_cast<const float*>(smem + L.off_bias());
+      const float* alpha = reinterpret_cast<const float*>(smem + L.off_alpha());
+      const DecodeArgs& D = work.m.d;
+      const int nout = work.m.nout;
+      int64_t tile[kSlots];
+      int stg[kSlots];
+
+      // features of slot s's current tile -> A0, then A-ready
+      auto start_tile = [&](int s) {
+        const int q = wg * kSlots + s;
+        unsigned char* slot = smem + S.slots + q * S.slot;
+        const uint32_t a0 = sbase + S.slots + q * S.slot + S.a0;
+        float f[12];
+        if (grid_chunk) {
+          const int64_t t0 = tile_first_texel(D, footprint, work.c.first + tile[s]);
+          if (footprint) {
+            // Ah is free: the previous tile's last MMA (which read it) has completed
+            footprint_features<kTile>(D, t0, gt, reinterpret_cast<float4*>(slot + S.ah), bar_id, f);
+          } else {
+            const int64_t tex = t0 + gt;
+            direct_features(D, tex < D.n ? tex : D.n - 1, f);
+          }
+        } else {
+          const int64_t px = frame_pixel(p, work.c, tile[s], gt);
+          const int64_t pq = px < 0 ? 0 : px;
+          const float2 uv = __ldg(reinterpret_cast<const float2*>(p.fuv) + pq);
+          trilinear_features(work.m, uv.x, uv.y, __ldg(p.flod + pq), f);
+        }
+        if constexpr (!FP8) {
+          sts128(a0 + off_interleave(gt, 0), cvt_f16x2(f[0], f[1]), cvt_f16x2(f[2], f[3]), cvt_f16x2(f[4], f[5]),
+                 cvt_f16x2(f[6], f[7]));
+          sts128(a0 + off_interleave(gt, 16), cvt_f16x2(f[8], f[9]), cvt_f16x2(f[10], f[11]),
+                 0x3C00u /* k = 12: 1.0 for the bias */, 0u);
+        } else {
+          const float is = alpha[NHID + 1];  // 1 / input scale
+          uint32_t w[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            w[i] = (uint32_t)cvt_e4m3x2(f[4 * i] * is, f[4 * i + 1] * is) |
+                   ((uint32_t)cvt_e4m3x2(f[4 * i + 2] * is, f[4 * i + 3] * is) << 16);
+          sts128(a0 + off_interleave(gt, 0), w[0], w[1], w[2], 0u);
+          sts128(a0 + off_interleave(gt, 16), 0u, 0u, 0u, 0u);
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(abar0 + q * 8);
+        stg[s] = 0;
+      };
+
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        tile[s] = wg * kSlots + s;
+        stg[s] = 0;
+        if (tile[s] < range_end) start_tile(s);
+      }
+      for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+          if (tile[s] >= range_end) continue;
+          any = true;
+          const int q = wg * kSlots + s;
+          if (!failed) failed = !mbar_wait_bounded(dbar0 + q * 8, dph[s], p.budget);
+          dph[s] ^= 1u;
+          failed = __any_sync(0xffffffffu, failed);  // warp-uniform: tcgen05.ld is .sync.aligned
+          tc_fence_after();
+          const uint32_t taddr = tmem_base + (uint32_t)(q * kHid) + lane_off;
+          if (stg[s] < NHID) {
+            // ---- hidden epilogue: accumulator -> (bias,) ReLU -> narrow -> Ah
+            const uint32_t ah = sbase + S.slots + q * S.slot + S.ah;
+            const float alp = alpha[stg[s]];
+            const float* b = bias + stg[s] * kHid;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              uint32_t r[32];
+              if (!failed) {
+                tmem_ld16(taddr + 32 * half, r);
+                tmem_ld16(taddr + 32 * half + 16, r + 16);
+                tmem_wait_ld32(r);
+              }
+              if constexpr (!FP8) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  const int j = 8 * c;
+                  sts128(ah + off_sw128(gt, 16 * (4 * half + c)),
+                         cvt_relu_f16x2(__uint_as_float(r[j + 0]), __uint_as_float(r[j + 1])),
+                         cvt_relu_f16x2(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])),
+                         cvt_relu_f16x2(__uint_as_float(r[j + 4]), __uint_as_float(r[j + 5])),
+                         cvt_relu_f16x2(__uint_as_float(r[j + 6]), __uint_as_float(r[j + 7])));
+                }
+              } else {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                  uint32_t w[4];
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                    const int j = 16 * c + 4 * e, jj = 32 * half + j;
+                    w[e] = (uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j]), alp, b[jj]),
+                                                     fmaf(__uint_as_float(r[j + 1]), alp, b[jj + 1])) |
+                           ((uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j + 2]), alp, b[jj + 2]),
+                                                      fmaf(__uint_as_float(r[j + 3]), alp, b[jj + 3]))
+                            << 16);
+                  }
+                  sts128(ah + off_sw64(gt, 16 * (2 * half + c)), w[0], w[1], w[2], w[3]);
+                }
+              }
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            mbar_arrive(abar0 + q * 8);
+            ++stg[s];
+          } else {
+            // ---- output epilogue: accumulator -> FP16 -> global
+            uint32_t r[16];
+            if (!failed) {
+              tmem_ld16(taddr, r);
+              tmem_wait_ld16(r);
+            }
+            tc_fence_before();
+            const float alp = alpha[NHID];
+            const float* b = bias + NHID * kHid;
+            uint16_t hv[kMaxOut];
+#pragma unroll
+            for (int k = 0; k < kMaxOut; ++k)
+              hv[k] = __half_as_ushort(FP8 ? __float2half_rn(fmaf(__uint_as_float(r[k]), alp, b[k]))
+                                           : __float2half_rn(__uint_as_float(r[k])));
+            if (grid_chunk) {
+              const int64_t t0 = tile_first_texel(D, footprint, work.c.first + tile[s]);
+              const int64_t tex = t0 + gt;
+              if (t0 + kTile <= D.n) {  // per-warp coalesced: 32 texels x nout halves
+                uint16_t* st = reinterpret_cast<uint16_t*>(stage_w);
+#pragma unroll
+                for (int k = 0; k < kMaxOut; ++k)
+                  if (k < nout) st[lane * nout + k] = hv[k];
+                __syncwarp();
+                const int n16 = 4 * nout;  // 32 texels x nout x 2 B / 16 B
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(D.out) + (t0 + 32 * wq) * nout);
+                const uint4* src = reinterpret_cast<const uint4*>(stage_w);
+                for (int c = lane; c < n16; c += 32) dst[c] = src[c];
+                __syncwarp();
+              } else if (tex < D.n) {
+                uint16_t* o = reinterpret_cast<uint16_t*>(D.out) + tex * nout;
+#pragma unroll
+                for (int k = 0; k < kMaxOut; ++k)
+                  if (k < nout) o[k] = hv[k];
+              }
+            } else {
+              const int64_t px = frame_pixel(p, work.c, tile[s], gt);
+              if (px >= 0) {
+                uint16_t* o = p.fout + px * nout;
+#pragma unroll
+                for (int k = 0; k < kMaxOut; ++k)
+                  if (k < nout) o[k] = hv[k];
+              }
+            }
+            tile[s] += NS;
+            if (tile[s] < range_end) start_tile(s);
+          }
+        }
+        if (!any) break;
+      }
+    }
+    // chunk end: every MMA of this chunk has been consumed; the MLP image and the
+    // material view may change
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  if (failed && tid == 0) record_status(status, NBTC_ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem_base, kTmemCols);
+}
+
+
+template <int NHID, bool FP8, int W>
+nbtc_status launch_tc_w(const TcArgs& p, int grid, cudaStream_t s) {
+  const TcSmem S = tc_smem(TcLayout{NHID, FP8}, W);
+  auto kern = k_decode_tc<NHID, FP8, W>;
+  nbtc_status st =
+      cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S.total), "smem attribute");
+  if (st) return st;
+  kern<<<grid, W * kTile + 32 * kMmaWarps, S.total, s>>>(p);
+  return cuda_check(cudaGetLastError(), "launch k_decode_tc");
+}
+
+}  // namespace nbtc

@@ -142,8 +142,12 @@ def he_mlp(rng: Rng, dims) -> Mlp:
 
 
 def full_mips(side: int) -> int:
-    """Mips of a square BC1 texture down to one 4x4 block."""
-    return int(math.log2(side // 4)) + 1
+    """Mips of a square BC1 texture: halve while the side stays a multiple of 4
+    (every mip then tiles into whole 4x4 blocks; a power-of-two side ends at 4x4)."""
+    m = 1
+    while (side >> m) >= 4 and (side >> m) % 4 == 0 and (side >> (m - 1)) % 2 == 0:
+        m += 1
+    return m
 
 
 def latent_pyramid(rng: Rng, side: int, mips: bool = False) -> list:
@@ -275,6 +279,7 @@ class BatchWorkload:
     uv: np.ndarray        # [frame_h, frame_w, 2] FP32
     lod_bias: np.ndarray  # [frame_h, frame_w] FP32
     seed: int
+    lod: np.ndarray = None  # [frame_h, frame_w] FP32: log2(uv footprint of a pixel) + bias
 
 
 def voronoi_ids(rng: Rng, w: int, h: int, m: int):
@@ -314,5 +319,7 @@ def batch_workload(num_materials: int = 64, frame_w: int = 3840, frame_h: int = 
     s_pix = scale[ids]
     uv = np.stack([s_pix * px / frame_h, s_pix * py / frame_h], axis=-1).astype(np.float32)
     bias = rng_f.uniform(frame_w * frame_h, 0.0, 3.0).reshape(frame_h, frame_w).astype(np.float32)
+    # a pixel spans s_m / frame_h in uv (tiled uv of scale s_m over the frame height)
+    lod = (bias.astype(np.float64) + np.log2(s_pix / frame_h)).astype(np.float32)
     return BatchWorkload(f"batch-{num_materials}mat-{frame_w}x{frame_h}", mats, sizes, frame_w, frame_h,
-                         ids, uv, bias, seed)
+                         ids, uv, bias, seed, lod)

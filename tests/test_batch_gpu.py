@@ -1,0 +1,137 @@
+"""GPU parity of the batched multi-material decode and the frame pipeline
+(Sec. 4, Algorithm 1) against the oracle: every material's FP16 full decode,
+every frame pixel's decode, the tile classification counts."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import require_gpu
+from test_decode_tc_gpu import _check
+
+pytestmark = pytest.mark.gpu
+NAN16 = 0x7E00
+# Share of outputs within one FP16 ulp of the emulator.  Trilinear features take
+# more FP32 steps than the single-level path, so an FP32 feature lands on the
+# other side of an FP16 rounding boundary more often; the per-output error bound
+# (checked first) is unchanged.  A systematic fault would miss this by far.
+FRAC = 0.95
+
+
+def FEATURE_BOUND(n):
+    """Latent features lie in [0, 1], so the network run on ones bounds the
+    magnitudes that enter the kernel-vs-emulator error bound."""
+    return np.ones((n, 12))
+
+
+@pytest.fixture(scope="module")
+def nb():
+    require_gpu()
+    import paper_2506_06040_gb300 as nb
+    return nb
+
+
+@pytest.fixture(scope="module")
+def ctx(nb):
+    c = nb.Context(0)
+    yield c
+    c.close()
+
+
+def _grid_check(mat, S, got, idx):
+    uv = np.stack([(idx % S + 0.5) / S, (idx // S + 0.5) / S], -1)
+    lod = np.full(len(idx), -64.0)   # mip 0 of every level
+    emu = oracle.frame.decode_pixels_direct(mat, uv, lod, "fp16")
+    _check(got, emu, mat, FEATURE_BOUND(len(idx)), 2.0 ** -10, FRAC)
+
+
+def _frame_tensors(bw, nout=9):
+    h, w = bw.frame_h, bw.frame_w
+    out = torch.full((h, w, nout), 0, dtype=torch.int16, device="cuda")
+    out.fill_(NAN16)
+    return {"mat_id": torch.from_numpy(bw.mat_id.astype(np.int32)).cuda(),
+            "uv": torch.from_numpy(np.ascontiguousarray(bw.uv)).cuda(),
+            "lod": torch.from_numpy(np.ascontiguousarray(bw.lod)).cuda(),
+            "out": out.view(torch.float16)}
+
+
+def _frame_check(bw, out, pixels):
+    got = out.view(-1, 9)[torch.from_numpy(pixels).cuda()].float().cpu().numpy().astype(np.float64)
+    ids = bw.mat_id.reshape(-1)[pixels]
+    uv = bw.uv.reshape(-1, 2)[pixels]
+    lod = bw.lod.reshape(-1)[pixels]
+    for m in np.unique(ids[ids >= 0]):
+        sel = ids == m
+        mat = bw.materials[m]
+        emu = oracle.frame.decode_pixels_direct(mat, uv[sel], lod[sel], "fp16")
+        _check(got[sel], emu, mat, FEATURE_BOUND(int(sel.sum())), 2.0 ** -10, FRAC)
+    raw = out.view(torch.int16).view(-1, 9)[torch.from_numpy(pixels).cuda()].cpu().numpy()
+    assert np.all(raw[ids < 0] == NAN16)  # pixels without a material are left untouched
+
+
+def _make(nb, ctx, bw, frame=True, autotune=True):
+    mats = [nb.Material.from_synth(m) for m in bw.materials]
+    outs = [(torch.empty((S * S, 9), dtype=torch.float16, device="cuda"), S, S) for S in bw.sizes]
+    fr = _frame_tensors(bw) if frame else None
+    plan = nb.Batch(ctx, mats, outs, fr, autotune=autotune)
+    return plan, mats, outs, fr
+
+
+def test_small_batch_decode_and_frame(nb, ctx):
+    bw = synth.batch_workload(num_materials=8, frame_w=512, frame_h=256, smin=256, smax=1024, seed=2024)
+    bw.mat_id[np.random.default_rng(1).random(bw.mat_id.shape) < 0.03] = -1   # pixels without material
+    plan, mats, outs, fr = _make(nb, ctx, bw)
+    plan.decode()
+    plan.render()
+    ctx.sync()
+    rng = np.random.default_rng(3)
+    for m, (S, mat) in enumerate(zip(bw.sizes, bw.materials)):
+        idx = np.concatenate([rng.integers(0, S * S, 1500), np.arange(S)])
+        got = outs[m][0][torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
+        _grid_check(mat, S, got, idx)
+    _frame_check(bw, fr["out"], np.arange(bw.frame_w * bw.frame_h))
+    # classification counts (Algorithm 1 pass A/B) for the tile shape the plan picked
+    info = plan.info()
+    kind, _ = oracle.frame.classify(bw.mat_id, info["tile_w"], info["tile_h"])
+    counts, _ = oracle.frame.mixed_counts(bw.mat_id, kind, info["tile_w"], info["tile_h"], len(bw.materials))
+    assert info["frame_uniform_tiles"] == int(np.sum(kind == oracle.frame.UNIFORM))
+    assert info["frame_mixed_tiles"] == int(np.sum(kind == oracle.frame.MIXED))
+    assert info["frame_packed_tiles"] == int(np.sum((counts + 127) // 128))
+    # graph replay gives the same frame
+    first = fr["out"].clone()
+    plan.render()
+    ctx.sync()
+    assert torch.equal(first.view(torch.int16), fr["out"].view(torch.int16))
+    plan.close()
+
+
+@pytest.mark.parametrize("shape", [(16, 8), (128, 1)])
+def test_frame_without_autotune_all_pixels(nb, ctx, shape):
+    bw = synth.batch_workload(num_materials=5, frame_w=256, frame_h=128, smin=256, smax=512, seed=77)
+    mats = [nb.Material.from_synth(m) for m in bw.materials]
+    fr = _frame_tensors(bw)
+    plan = nb.Batch(ctx, mats, None, fr, autotune=False)
+    plan.render()
+    ctx.sync()
+    _frame_check(bw, fr["out"], np.arange(bw.frame_w * bw.frame_h))
+    plan.close()
+
+
+def test_full_size_batch(nb, ctx):
+    """64 materials of 256^2..4096^2 and a 3840x2160 frame, as the benchmark runs
+    them: sampled texels of every material and 20,000 frame pixels."""
+    bw = synth.batch_workload()
+    plan, mats, outs, fr = _make(nb, ctx, bw)
+    plan.decode()
+    plan.render()
+    ctx.sync()
+    rng = np.random.default_rng(4)
+    for m, (S, mat) in enumerate(zip(bw.sizes, bw.materials)):
+        idx = rng.integers(0, S * S, 300)
+        got = outs[m][0][torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
+        _grid_check(mat, S, got, idx)
+    _frame_check(bw, fr["out"], rng.integers(0, bw.frame_w * bw.frame_h, 20000))
+    info = plan.info()
+    assert info["decode_tiles"] == sum(S * S // 128 for S in bw.sizes)
+    plan.close()

@@ -49,3 +49,18 @@ def test_pixel_decode_at_mip0_equals_grid_decode():
     got = frame.decode_pixels(mat, mips, uv, np.full(n, -20.0), precision="fp64")
     want = decode.decode_grid(mat, 256, 256, idx)
     np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def test_direct_pixel_decode_equals_full_mip_decode():
+    """Tap-on-demand BC1 sampling gives the same frame decode as sampling fully decoded mips."""
+    bw = synth.batch_workload(num_materials=3, frame_w=64, frame_h=32, smin=256, smax=512)
+    rng = np.random.default_rng(9)
+    for mat in bw.materials:
+        mips = [frame.level_mips_rgb(lv) for lv in mat.levels]
+        n = 400
+        uv = rng.uniform(-2, 6, size=(n, 2))
+        lod = rng.uniform(-12, 2, size=n)
+        for prec in ("fp64", "fp16"):
+            a = frame.decode_pixels(mat, mips, uv, lod, precision=prec)
+            b = frame.decode_pixels_direct(mat, uv, lod, precision=prec)
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
