@@ -232,6 +232,33 @@ def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
                          "note": "whole step (forward, backward, reduction, Adam) against the FP32 FFMA peak"}}
 
 
+def run_batch(args, nb, ctx, stream, flush) -> dict:
+    """64 materials (sides log-uniform 256..4096, each its own BC1 pyramid with
+    mips and FP16 MLP 12-64-64-9): the full decode of all of them in one graph
+    launch, and a 3840x2160 frame (Voronoi material ids, tiled uv, mip bias)
+    through classification, binning and the trilinear decode."""
+    import torch
+    bw = synth.batch_workload()
+    mats = [nb.Material.from_synth(m) for m in bw.materials]
+    outs = [(torch.empty((S * S, 9), dtype=torch.float16, device="cuda"), S, S) for S in bw.sizes]
+    fr = {"mat_id": torch.from_numpy(bw.mat_id.astype(np.int32)).cuda(),
+          "uv": torch.from_numpy(np.ascontiguousarray(bw.uv)).cuda(),
+          "lod": torch.from_numpy(np.ascontiguousarray(bw.lod)).cuda(),
+          "out": torch.empty((bw.frame_h, bw.frame_w, 9), dtype=torch.float16, device="cuda")}
+    plan = nb.Batch(ctx, mats, outs, fr, autotune=True, stream=stream)
+    texels = sum(S * S for S in bw.sizes)
+    td = _time_steps(lambda: plan.decode(stream), max(3, args.steps // 4), args.warmup, flush, stream)
+    tr = _time_steps(lambda: plan.render(stream), args.steps, args.warmup, flush, stream)
+    info = plan.info()
+    ctx.sync(stream)
+    plan.close()
+    pixels = bw.frame_w * bw.frame_h
+    return {"workload": bw.name, "materials": len(bw.materials), "decode_texels": texels,
+            "decode_gtexel_s": texels / statistics.mean(td) / 1e6, "decode_ms": statistics.mean(td),
+            "frame": f"{bw.frame_w}x{bw.frame_h}", "frame_ms": statistics.mean(tr),
+            "frame_gpx_s": pixels / statistics.mean(tr) / 1e6, "plan": info}
+
+
 def run_ours(args) -> dict | None:
     import torch
 
@@ -333,6 +360,8 @@ def run_ours(args) -> dict | None:
         res["forms"] = run_forms(args, nb, ctx, stream, flush, peaks, sm_count)
     if "train" in args.parts:
         res["train"] = run_train(args, nb, ctx, stream, flush, sm_count, peaks)
+    if "batch" in args.parts:
+        res["batch"] = run_batch(args, nb, ctx, stream, flush)
     ctx.close()
     if world > 1:
         import torch.distributed as dist
@@ -370,7 +399,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--parts", default="main,forms,train", help="comma list: main (always), forms, train")
+    ap.add_argument("--parts", default="main,forms,train,batch",
+                    help="comma list: main (always), forms, train, batch")
     ap.add_argument("--form-side", type=int, default=4096, help="output side of the precision-form workload")
     ap.add_argument("--side", type=int, default=4096, help="output side (4096 = the benchmark workload; "
                     "smaller sides are for profiling captures)")

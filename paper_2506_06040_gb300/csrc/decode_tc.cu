@@ -147,10 +147,22 @@ nbtc_status launch_tc_h2_f16(const TcArgs& p, int W, int grid, cudaStream_t s);
 nbtc_status launch_tc_h2_f8(const TcArgs& p, int W, int grid, cudaStream_t s);
 nbtc_status launch_tc_h3_f16(const TcArgs& p, int W, int grid, cudaStream_t s);
 nbtc_status launch_tc_h3_f8(const TcArgs& p, int W, int grid, cudaStream_t s);
+nbtc_status launch_tc_h1_f16_batch(const TcArgs& p, int W, int grid, cudaStream_t s);
+nbtc_status launch_tc_h2_f16_batch(const TcArgs& p, int W, int grid, cudaStream_t s);
+nbtc_status launch_tc_h3_f16_batch(const TcArgs& p, int W, int grid, cudaStream_t s);
 
 nbtc_status launch_tc_args(nbtc_context* ctx, const TcArgs& p, int nhid, bool fp8, int W, int grid, cudaStream_t s) {
   (void)ctx;
   if (W != 3 && W != 4) return fail(NBTC_ERR_UNSUPPORTED, "tensor-core decode takes 3 or 4 warpgroups");
+  if (p.mode == kModeBatch) {
+    if (fp8) return fail(NBTC_ERR_UNSUPPORTED, "batched decode runs the FP16 form");
+    switch (nhid) {
+      case 1: return launch_tc_h1_f16_batch(p, W, grid, s);
+      case 2: return launch_tc_h2_f16_batch(p, W, grid, s);
+      case 3: return launch_tc_h3_f16_batch(p, W, grid, s);
+    }
+    return fail(NBTC_ERR_UNSUPPORTED, "tensor-core decode takes 1..3 hidden layers");
+  }
   switch (nhid) {
     case 1: return fp8 ? launch_tc_h1_f8(p, W, grid, s) : launch_tc_h1_f16(p, W, grid, s);
     case 2: return fp8 ? launch_tc_h2_f8(p, W, grid, s) : launch_tc_h2_f16(p, W, grid, s);

@@ -4,7 +4,7 @@
 namespace nbtc {
 
 nbtc_status launch_tc_h1_f8(const TcArgs& p, int W, int grid, cudaStream_t s) {
-  return W == 3 ? launch_tc_w<1, true, 3>(p, grid, s) : launch_tc_w<1, true, 4>(p, grid, s);
+  return W == 3 ? launch_tc_w<1, true, 3, kModeSingle>(p, grid, s) : launch_tc_w<1, true, 4, kModeSingle>(p, grid, s);
 }
 
 }  // namespace nbtc

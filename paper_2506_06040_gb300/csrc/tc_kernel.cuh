@@ -93,7 +93,9 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W) {
 //   D-ready[q]  (tcgen05.commit): that layer's accumulator is in TMEM
 // After a timeout a thread stops waiting but keeps its schedule (every
 // barrier and arrival still happens), so the kernel always terminates.
-template <int NHID, bool FP8, int W>
+// MODE kModeSingle: one material whose views are kernel parameters; kModeBatch:
+// chunks of many materials (and frame tiles) whose views live in shared memory.
+template <int NHID, bool FP8, int W, int MODE>
 __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArgs p) {
   constexpr TcLayout L{NHID, FP8};
   constexpr int NS = W * kSlots;
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
     // ---- take the next chunk (thread 0), load its material's MLP if it changed
     if (tid == 0) {
       int valid = 0, reload = 0;
-      if (p.mode == kModeSingle) {
+      if (MODE == kModeSingle) {
         if (first_chunk) {
           const int64_t b = (int64_t)blockIdx.x * p.per_cta;
           const int64_t e = b + p.per_cta < p.tiles ? b + p.per_cta : p.tiles;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
     }
     failed = __syncthreads_or(failed);
     const bool grid_chunk = work.c.kind == kChunkGrid;
-    const bool footprint = p.mode == kModeSingle ? p.footprint != 0 : grid_chunk;
+    const bool footprint = MODE == kModeSingle ? p.footprint != 0 : grid_chunk;
     const int64_t range_end = work.c.count;   // tiles are numbered 0 .. count-1 inside the chunk
 
     if (warp >= 4 * W) {
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
       unsigned char* stage_w = smem + S.stage + warp * kStageBytes;
       const float* bias = reinterpret_cast<const float*>(smem + L.off_bias());
       const float* alpha = reinterpret_cast<const float*>(smem + L.off_alpha());
-      const DecodeArgs& D = work.m.d;
+      const DecodeArgs& D = MODE == kModeSingle ? p.d : work.m.d;
       const int nout = work.m.nout;
       int64_t tile[kSlots];
       int stg[kSlots];
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
         unsigned char* slot = smem + S.slots + q * S.slot;
         const uint32_t a0 = sbase + S.slots + q * S.slot + S.a0;
         float f[12];
-        if (grid_chunk) {
+        if (MODE == kModeSingle || grid_chunk) {
           const int64_t t0 = tile_first_texel(D, footprint, work.c.first + tile[s]);
           if (footprint) {
             // Ah is free: the previous tile's last MMA (which read it) has completed
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
             for (int k = 0; k < kMaxOut; ++k)
               hv[k] = __half_as_ushort(FP8 ? __float2half_rn(fmaf(__uint_as_float(r[k]), alp, b[k]))
                                            : __float2half_rn(__uint_as_float(r[k])));
-            if (grid_chunk) {
+            if (MODE == kModeSingle || grid_chunk) {
               const int64_t t0 = tile_first_texel(D, footprint, work.c.first + tile[s]);
               const int64_t tex = t0 + gt;
               if (t0 + kTile <= D.n) {  // per-warp coalesced: 32 texels x nout halves
@@ -448,10 +450,10 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
 }
 
 
-template <int NHID, bool FP8, int W>
+template <int NHID, bool FP8, int W, int MODE>
 nbtc_status launch_tc_w(const TcArgs& p, int grid, cudaStream_t s) {
   const TcSmem S = tc_smem(TcLayout{NHID, FP8}, W);
-  auto kern = k_decode_tc<NHID, FP8, W>;
+  auto kern = k_decode_tc<NHID, FP8, W, MODE>;
   nbtc_status st =
       cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S.total), "smem attribute");
   if (st) return st;
