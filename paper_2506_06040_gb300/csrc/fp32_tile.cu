@@ -1,0 +1,203 @@
+// FP32 SIMT form of the fused decode as a tiled GEMM (hidden width 64).
+//
+// A CTA of 256 threads decodes tiles of 256 consecutive output texels of one
+// row: the footprint feature stage (features.cuh) writes the 12 features of the
+// tile feature-major into shared memory, then every layer is a register-blocked
+// FP32 GEMM over the tile -- each thread owns 8 texels x 8 neurons (64 FFMA per
+// k step from two 128-bit activation loads and two broadcast 128-bit weight
+// loads), hidden activations are rewritten in place between layers, and the
+// output layer's rows are staged for coalesced 128-bit stores.  True FP32 FFMA
+// throughout (the plain FP32 form of the method, Sec. 5 "software FMA").
+#include "features.cuh"
+#include "host.h"
+
+namespace nbtc {
+
+namespace {
+
+constexpr int kT = 256;      // texels per tile = threads per CTA
+constexpr int kD = 64;       // hidden width
+constexpr int kIn = 12;
+constexpr int kOutMax = 16;
+
+template <int NHID>
+struct TileSmem {
+  float w1t[kIn * kD];                 // [k][n]
+  float wht[(NHID - 1) * kD * kD];     // hidden->hidden, [k][n] per layer (NHID-1 >= 0)
+  float wot[kD * kOutMax];             // [k][c]
+  float b[NHID * kD + kOutMax];
+  float x[kOutMax * kT];               // features [k][texel]; reused as output staging [texel][c]
+  float h[kD * kT];                    // activations [n][texel]; reused as the column buffer
+};
+
+// acc[i][j] = sum_k A[k][8 sg + i] * Bt[k][8 ng + j]
+template <int K>
+__device__ __forceinline__ void gemm8x8(const float* __restrict__ A, const float* __restrict__ Bt, int sg, int ng,
+                                        float (&acc)[8][8]) {
+#pragma unroll 2
+  for (int k = 0; k < K; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kT + 8 * sg);
+    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kT + 8 * sg + 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bt + k * kD + 8 * ng);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bt + k * kD + 8 * ng + 4);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+__device__ __forceinline__ void store_relu(float* __restrict__ H, int sg, int ng, const float (&acc)[8][8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float4* row = reinterpret_cast<float4*>(H + (8 * ng + j) * kT + 8 * sg);
+    row[0] = make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
+    row[1] = make_float4(fmaxf(acc[4][j], 0.f), fmaxf(acc[5][j], 0.f), fmaxf(acc[6][j], 0.f), fmaxf(acc[7][j], 0.f));
+  }
+}
+
+template <int NHID>
+__global__ void __launch_bounds__(kT, 2) k_decode_fp32_tile(DecodeArgs a, const float* __restrict__ gW,
+                                                           const float* __restrict__ gB, int nout, int footprint) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem<NHID>& S = *reinterpret_cast<TileSmem<NHID>*>(smem_raw);
+  const int t = threadIdx.x;
+  // ---- weights: global [out][in] per layer -> shared [in][out]
+  {
+    int off = 0;
+    for (int e = t; e < kD * kIn; e += kT) {
+      const int n = e / kIn, k = e - n * kIn;
+      S.w1t[k * kD + n] = gW[e];
+    }
+    off += kD * kIn;
+    for (int l = 0; l < NHID - 1; ++l) {
+      for (int e = t; e < kD * kD; e += kT) {
+        const int n = e / kD, k = e - n * kD;
+        S.wht[l * kD * kD + k * kD + n] = gW[off + e];
+      }
+      off += kD * kD;
+    }
+    for (int e = t; e < kD * kOutMax; e += kT) {
+      const int c = e / kD, k = e - c * kD;
+      S.wot[k * kOutMax + c] = c < nout ? gW[off + c * kD + k] : 0.f;
+    }
+    for (int e = t; e < NHID * kD + kOutMax; e += kT) S.b[e] = e < NHID * kD + nout ? gB[e] : 0.f;
+  }
+  __syncthreads();
+  const int sg = t & 31, ng = t >> 5;  // warp = 8-neuron group (weights broadcast), lane = 8-texel group
+  const int64_t tiles = (a.n + kT - 1) / kT;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t t0 = tile * kT;
+    // ---- features -> x [k][texel]
+    float f[12];
+    if (footprint) {
+      footprint_features<kT>(a, t0, t, reinterpret_cast<float4*>(S.h), 1, f);
+    } else {
+      const int64_t tex = t0 + t;
+      direct_features(a, tex < a.n ? tex : a.n - 1, f);
+    }
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) S.x[k * kT + t] = f[k];
+    __syncthreads();
+    // ---- layer 1
+    {
+      float acc[8][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = S.b[8 * ng + j];
+      gemm8x8<kIn>(S.x, S.w1t, sg, ng, acc);
+      store_relu(S.h, sg, ng, acc);
+    }
+    __syncthreads();
+    // ---- hidden layers, in place
+#pragma unroll 1
+    for (int l = 0; l < NHID - 1; ++l) {
+      float acc[8][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = S.b[(l + 1) * kD + 8 * ng + j];
+      gemm8x8<kD>(S.h, S.wht + l * kD * kD, sg, ng, acc);
+      __syncthreads();
+      store_relu(S.h, sg, ng, acc);
+      __syncthreads();
+    }
+    // ---- output layer: thread t -> texel t, all channels; staged in x
+    {
+      float y[kOutMax];
+#pragma unroll
+      for (int c = 0; c < kOutMax; ++c) y[c] = S.b[NHID * kD + c];
+#pragma unroll 4
+      for (int k = 0; k < kD; ++k) {
+        const float hv = S.h[k * kT + t];
+        const float4* w = reinterpret_cast<const float4*>(S.wot + k * kOutMax);
+#pragma unroll
+        for (int q = 0; q < kOutMax / 4; ++q) {
+          const float4 wq = w[q];
+          y[4 * q + 0] = fmaf(wq.x, hv, y[4 * q + 0]);
+          y[4 * q + 1] = fmaf(wq.y, hv, y[4 * q + 1]);
+          y[4 * q + 2] = fmaf(wq.z, hv, y[4 * q + 2]);
+          y[4 * q + 3] = fmaf(wq.w, hv, y[4 * q + 3]);
+        }
+      }
+      // x (features) is free: every thread passed the layer-1 barrier
+#pragma unroll
+      for (int c = 0; c < kOutMax; ++c)
+        if (c < nout) S.x[t * nout + c] = y[c];
+    }
+    __syncthreads();
+    {
+      float* out = reinterpret_cast<float*>(a.out);
+      const int64_t valid = a.n - t0 < kT ? a.n - t0 : kT;
+      if (valid == kT) {  // whole tile: 256 * nout contiguous floats, 16-byte aligned
+        const float4* src = reinterpret_cast<const float4*>(S.x);
+        float4* dst = reinterpret_cast<float4*>(out + t0 * nout);
+        for (int e = t; e < kT * nout / 4; e += kT) dst[e] = src[e];
+      } else {
+        for (int e = t; e < valid * nout; e += kT) out[t0 * nout + e] = S.x[e];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int NHID>
+nbtc_status launch_tile(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, int footprint, cudaStream_t s) {
+  const size_t smem = sizeof(TileSmem<NHID>);
+  auto kern = k_decode_fp32_tile<NHID>;
+  nbtc_status st =
+      cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
+  if (st) return st;
+  int per_sm = 0;
+  if ((st = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, smem), "occupancy")))
+    return st;
+  const int64_t tiles = (a.n + kT - 1) / kT;
+  int64_t grid = (int64_t)ctx->sm_count * (per_sm > 0 ? per_sm : 1);
+  if (grid > tiles) grid = tiles;
+  kern<<<(int)grid, kT, smem, s>>>(a, mlp->weights, mlp->biases, mlp->dims[mlp->num_layers], footprint);
+  return cuda_check(cudaGetLastError(), "launch k_decode_fp32_tile");
+}
+
+}  // namespace
+
+// Tiled FP32 decode for MLPs [12, 64, .., 64, C <= 16] (1-3 hidden layers);
+// returns NBTC_ERR_UNSUPPORTED (without launching) for other shapes.
+nbtc_status launch_decode_fp32_tile(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, cudaStream_t s) {
+  const int L = mlp->num_layers;
+  if (mlp->dims[0] != kIn || L < 2 || L > 4 || mlp->dims[L] > kOutMax) return NBTC_ERR_UNSUPPORTED;
+  for (int l = 1; l < L; ++l)
+    if (mlp->dims[l] != kD) return NBTC_ERR_UNSUPPORTED;
+  // footprint stage: tiles inside one output row, every level's span within the column buffer
+  bool fp = a.uv == nullptr && (a.grid_w % kT) == 0;
+  for (int k = 0; k < 4; ++k) fp = fp && (int64_t)(kT - 1) * a.lv[k].w / a.grid_w + 3 <= kColCap;
+  switch (L - 1) {
+    case 1: return launch_tile<1>(ctx, a, mlp, fp, s);
+    case 2: return launch_tile<2>(ctx, a, mlp, fp, s);
+    default: return launch_tile<3>(ctx, a, mlp, fp, s);
+  }
+}
+
+}  // namespace nbtc
