@@ -30,35 +30,54 @@ struct TileSmem {
   float h[kD * kT];                    // activations [n][texel]; reused as the column buffer
 };
 
-// acc[i][j] = sum_k A[k][8 sg + i] * Bt[k][8 ng + j]
+// Thread (sg, ng) owns texels 4 sg + {0..3} and 128 + 4 sg + {0..3} (so each
+// 128-bit activation load is contiguous across the warp: no bank conflicts)
+// and neurons 8 ng + {0..7}.  Accumulators are texel pairs (FP32x2): acc[i][j]
+// holds texels (2i, 2i+1) of the thread's 8 for neuron 8 ng + j, so every
+// multiply-add is one packed FMA (two IEEE FP32 FMAs) and a weight feeds two
+// texels per instruction.
 template <int K>
 __device__ __forceinline__ void gemm8x8(const float* __restrict__ A, const float* __restrict__ Bt, int sg, int ng,
-                                        float (&acc)[8][8]) {
+                                        float2 (&acc)[4][8]) {
 #pragma unroll 2
   for (int k = 0; k < K; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kT + 8 * sg);
-    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kT + 8 * sg + 4);
+    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kT + 4 * sg);
+    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kT + kT / 2 + 4 * sg);
     const float4 b0 = *reinterpret_cast<const float4*>(Bt + k * kD + 8 * ng);
     const float4 b1 = *reinterpret_cast<const float4*>(Bt + k * kD + 8 * ng + 4);
-    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float2 av[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                          make_float2(a1.z, a1.w)};
     const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) {
+      const float2 w = make_float2(bv[j], bv[j]);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int i = 0; i < 4; ++i) acc[i][j] = __ffma2_rn(av[i], w, acc[i][j]);
+    }
   }
 }
 
-__device__ __forceinline__ void store_relu(float* __restrict__ H, int sg, int ng, const float (&acc)[8][8]) {
+__device__ __forceinline__ void init_bias(const float* __restrict__ b, int ng, float2 (&acc)[4][8]) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    float4* row = reinterpret_cast<float4*>(H + (8 * ng + j) * kT + 8 * sg);
-    row[0] = make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
-    row[1] = make_float4(fmaxf(acc[4][j], 0.f), fmaxf(acc[5][j], 0.f), fmaxf(acc[6][j], 0.f), fmaxf(acc[7][j], 0.f));
+    const float v = b[8 * ng + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][j] = make_float2(v, v);
   }
 }
 
-template <int NHID>
+__device__ __forceinline__ void store_relu(float* __restrict__ H, int sg, int ng, const float2 (&acc)[4][8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float* row = H + (8 * ng + j) * kT;
+    *reinterpret_cast<float4*>(row + 4 * sg) = make_float4(fmaxf(acc[0][j].x, 0.f), fmaxf(acc[0][j].y, 0.f),
+                                                           fmaxf(acc[1][j].x, 0.f), fmaxf(acc[1][j].y, 0.f));
+    *reinterpret_cast<float4*>(row + kT / 2 + 4 * sg) = make_float4(fmaxf(acc[2][j].x, 0.f), fmaxf(acc[2][j].y, 0.f),
+                                                                    fmaxf(acc[3][j].x, 0.f), fmaxf(acc[3][j].y, 0.f));
+  }
+}
+
+template <int NHID, int NO>
 __global__ void __launch_bounds__(kT, 2) k_decode_fp32_tile(DecodeArgs a, const float* __restrict__ gW,
                                                            const float* __restrict__ gB, int nout, int footprint) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -103,11 +122,8 @@ __global__ void __launch_bounds__(kT, 2) k_decode_fp32_tile(DecodeArgs a, const 
     __syncthreads();
     // ---- layer 1
     {
-      float acc[8][8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = S.b[8 * ng + j];
+      float2 acc[4][8];
+      init_bias(S.b, ng, acc);
       gemm8x8<kIn>(S.x, S.w1t, sg, ng, acc);
       store_relu(S.h, sg, ng, acc);
     }
@@ -115,38 +131,32 @@ __global__ void __launch_bounds__(kT, 2) k_decode_fp32_tile(DecodeArgs a, const 
     // ---- hidden layers, in place
 #pragma unroll 1
     for (int l = 0; l < NHID - 1; ++l) {
-      float acc[8][8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = S.b[(l + 1) * kD + 8 * ng + j];
+      float2 acc[4][8];
+      init_bias(S.b + (l + 1) * kD, ng, acc);
       gemm8x8<kD>(S.h, S.wht + l * kD * kD, sg, ng, acc);
       __syncthreads();
       store_relu(S.h, sg, ng, acc);
       __syncthreads();
     }
-    // ---- output layer: thread t -> texel t, all channels; staged in x
+    // ---- output layer: thread t -> texel t, NO (padded) channels as FP32x2 pairs; staged in x
     {
-      float y[kOutMax];
+      float2 y[NO / 2];
 #pragma unroll
-      for (int c = 0; c < kOutMax; ++c) y[c] = S.b[NHID * kD + c];
+      for (int c = 0; c < NO / 2; ++c) y[c] = make_float2(S.b[NHID * kD + 2 * c], S.b[NHID * kD + 2 * c + 1]);
 #pragma unroll 4
       for (int k = 0; k < kD; ++k) {
         const float hv = S.h[k * kT + t];
-        const float4* w = reinterpret_cast<const float4*>(S.wot + k * kOutMax);
+        const float2 h2 = make_float2(hv, hv);
+        const float2* w = reinterpret_cast<const float2*>(S.wot + k * kOutMax);
 #pragma unroll
-        for (int q = 0; q < kOutMax / 4; ++q) {
-          const float4 wq = w[q];
-          y[4 * q + 0] = fmaf(wq.x, hv, y[4 * q + 0]);
-          y[4 * q + 1] = fmaf(wq.y, hv, y[4 * q + 1]);
-          y[4 * q + 2] = fmaf(wq.z, hv, y[4 * q + 2]);
-          y[4 * q + 3] = fmaf(wq.w, hv, y[4 * q + 3]);
-        }
+        for (int c = 0; c < NO / 2; ++c) y[c] = __ffma2_rn(w[c], h2, y[c]);
       }
       // x (features) is free: every thread passed the layer-1 barrier
 #pragma unroll
-      for (int c = 0; c < kOutMax; ++c)
-        if (c < nout) S.x[t * nout + c] = y[c];
+      for (int c = 0; c < NO / 2; ++c) {
+        if (2 * c < nout) S.x[t * nout + 2 * c] = y[c].x;
+        if (2 * c + 1 < nout) S.x[t * nout + 2 * c + 1] = y[c].y;
+      }
     }
     __syncthreads();
     {
@@ -167,7 +177,7 @@ __global__ void __launch_bounds__(kT, 2) k_decode_fp32_tile(DecodeArgs a, const 
 template <int NHID>
 nbtc_status launch_tile(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, int footprint, cudaStream_t s) {
   const size_t smem = sizeof(TileSmem<NHID>);
-  auto kern = k_decode_fp32_tile<NHID>;
+  auto kern = mlp->dims[mlp->num_layers] <= 10 ? k_decode_fp32_tile<NHID, 10> : k_decode_fp32_tile<NHID, 16>;
   nbtc_status st =
       cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
   if (st) return st;
