@@ -48,6 +48,32 @@ def _peaks() -> dict:
             "source": "fallback"}
 
 
+def _profiled_traffic(profile: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+    kernel, as recorded in profiles/<profile>.md from one ncu capture, or None
+    when the kernel's sources changed since (the summary stores the SHA-256 of
+    the source files it was captured from) or the summary is missing."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", profile + ".md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    try:
+        srcs = [s.strip() for s in fields["sources"].split(",")]
+        h = hashlib.sha256()
+        for src in srcs:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
+        if h.hexdigest() != fields["source_sha256"]:
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, OSError, ValueError):
+        return None
+
+
 def _fp32_peak_tflops(sm_count: int, mhz: float) -> float:
     """FFMA peak: SMs x 128 FP32 lanes x 2 FLOP x clock."""
     return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
@@ -200,7 +226,7 @@ def run_forms(args, nb, ctx, stream, flush, peaks, sm_count) -> dict:
         ach = flop * n / (ms * 1e-3) / 1e12
         res[name] = {"gtexel_s": n / ms / 1e6, "kernel_ms": ms, "max_abs_dev_vs_fp32_per_channel": err,
                      "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": ach / peak,
+                                  "frac": ach / peak, "traffic": _profiled_traffic(f"k_decode_tc_{name[:3]}_{W}sq"),
                                   "peak_source": "measured bf16 dense burst" + (" x 2 (fp8 nominal ratio)" if prec == nb.FP8_E4M3 else "")}}
     res["fp16_tc_speedup_vs_fp32"] = res["fp16_tc"]["gtexel_s"] / res["fp32"]["gtexel_s"]
     ctx.sync(stream)
@@ -348,9 +374,9 @@ def run_ours(args) -> dict | None:
                    "latent_levels": [1024, 512, 256, 128], "mlp": [12, 64, 64, 9], "parallelism": f"replicas{world}",
                    "l2": "256 MB buffer written between timed steps; the 604 MB output also exceeds L2"},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved_tf / peak_tf, "traffic": None,
+                     "frac": achieved_tf / peak_tf, "traffic": _profiled_traffic("k_decode_fp32_tile_4096sq"),
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
-                     "kernel": "k_decode_fp32<64,2,9,2>", "kernel_ms": kernel_ms},
+                     "kernel": "k_decode_fp32_tile<2,10>", "kernel_ms": kernel_ms},
         "e2e": {"value": e2e, "unit": "Gtexel/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clk,

@@ -12,6 +12,8 @@
 // per tap.  Direct mode (uv lists, ragged grids) samples each texel on its own.
 #pragma once
 
+#include <climits>
+
 #include "common.cuh"
 #include "sm100.cuh"
 
@@ -172,6 +174,101 @@ __device__ __forceinline__ void footprint_features(const DecodeArgs& a, int64_t 
   decode_columns<NT>(a, P, tid, pf, colbuf);
   sm100::named_bar_sync(bar_id, NT);
   blend_columns<NT>(a, P, tid, colbuf, feat);
+}
+
+// ---- row-footprint feature stage with a per-thread column cache, for a group
+// of NT threads that decodes vertically consecutive tiles of one column strip
+// (the same first column i0, output rows j, j+1, ...).  Across such tiles the
+// column plan, each thread's column job and each texel's horizontal taps stay
+// fixed, and a latent column's two vertical taps (rows floor(ty), floor(ty)+1)
+// change only when ty crosses a texel boundary: every 4th output row for a
+// latent at 1/4 of the output side, every 32nd at 1/32.  So each thread keeps
+// its job's two decoded texels (as floats scaled to [0, 1]) and reloads and
+// decodes the BC1 blocks only when floor(ty) changes; per tile it only redoes
+// the vertical blend of its column and the horizontal blend of its texel.
+struct StripCache {
+  int i0;          // first output column of the cached strip (-1: none)
+  int total;       // column jobs of the strip
+  int job;         // own job: level | colbuf slot << 2 (-1: none)
+  int jx;          // own job: latent column (wrapped or clamped)
+  int key;         // floor(ty) of the decoded pair (INT_MIN: none)
+  uint32_t rel4;   // own texel: left tap's colbuf slot per level, 8 bits each
+  float fx[4];     // own texel: horizontal weight per level
+  float c0[3];     // own job: texel (jx, y0), RGB / 255
+  float dc[3];     // own job: texel (jx, y1) minus texel (jx, y0), RGB / 255
+};
+
+__device__ __forceinline__ void strip_reset(StripCache& C) { C.i0 = -1; }
+
+// Features of texel i0 + tid of output row j; (j, i0) is a tile of NT texels
+// in one row (i0 + NT <= grid_w).
+template <int NT>
+__device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i0, int tid, uint32_t colbuf,
+                                               int bar_id, StripCache& C, float (&feat)[12]) {
+  const float s = 1.0f / 255.0f;
+  if (i0 != C.i0) {  // new strip: column plan, own job, own texel's taps
+    C.i0 = i0;
+    C.key = INT_MIN;
+    const float u0 = ((float)i0 + 0.5f) * a.inv_gw;
+    const float u1 = ((float)(i0 + NT - 1) + 0.5f) * a.inv_gw;
+    const float u = ((float)(i0 + tid) + 0.5f) * a.inv_gw;
+    int total = 0, job = -1, jx = 0;
+    uint32_t rel4 = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const LevelView& L = a.lv[k];
+      const int b0 = (int)floorf(texel_coord(u0, L.w, L.shift));
+      const int b1 = (int)floorf(texel_coord(u1, L.w, L.shift));
+      const int span = min(b1 - b0 + 2, kColCap);
+      if (tid >= total && tid < total + span) {
+        job = k | (tid - total) << 2;
+        jx = wrap_or_clamp(b0 + tid - total, L.w, a.wrap);
+      }
+      total += span;
+      const float tx = texel_coord(u, L.w, L.shift);
+      const float ftx = floorf(tx);
+      C.fx[k] = tx - ftx;
+      // floor is monotone in u, so the slot lies in [0, span - 2]; the clamp only guards the buffer
+      rel4 |= (uint32_t)min(max((int)ftx - b0, 0), span - 2) << (8 * k);
+    }
+    C.total = total;
+    C.job = job;
+    C.jx = jx;
+    C.rel4 = rel4;
+  }
+  if (C.job >= 0) {
+    const int k = C.job & 3;
+    const LevelView& L = a.lv[k];
+    const float ty = texel_coord(((float)j + 0.5f) * a.inv_gh, L.h, L.shift);
+    const float fty = floorf(ty);
+    const float fy = ty - fty;
+    const int key = (int)fty;
+    if (key != C.key) {
+      C.key = key;
+      const int y0 = wrap_or_clamp(key, L.h, a.wrap), y1 = wrap_or_clamp(key + 1, L.h, a.wrap);
+      const uint64_t* col = L.blocks + (C.jx >> 2);
+      const uint32_t t0 = bc1_texel(__ldg(col + (size_t)(y0 >> 2) * L.wb), C.jx & 3, y0 & 3);
+      const uint32_t t1 = bc1_texel(__ldg(col + (size_t)(y1 >> 2) * L.wb), C.jx & 3, y1 & 3);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v0 = (float)((t0 >> (8 * c)) & 255u), v1 = (float)((t1 >> (8 * c)) & 255u);
+        C.c0[c] = s * v0;
+        C.dc[c] = s * (v1 - v0);
+      }
+    }
+    sm100::sts128f(colbuf + 16u * (uint32_t)(k * kColCap + (C.job >> 2)), fmaf(fy, C.dc[0], C.c0[0]),
+                   fmaf(fy, C.dc[1], C.c0[1]), fmaf(fy, C.dc[2], C.c0[2]), 0.f);
+  }
+  sm100::named_bar_sync(bar_id, NT);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t at = colbuf + 16u * (uint32_t)(k * kColCap + ((C.rel4 >> (8 * k)) & 255));
+    const float4 A = sm100::lds128f(at);
+    const float4 B = sm100::lds128f(at + 16);
+    feat[3 * k + 0] = fmaf(C.fx[k], B.x - A.x, A.x);
+    feat[3 * k + 1] = fmaf(C.fx[k], B.y - A.y, A.y);
+    feat[3 * k + 2] = fmaf(C.fx[k], B.z - A.z, A.z);
+  }
 }
 
 // Per-material description used by the batched and frame decodes: the level

@@ -12,7 +12,7 @@ struct nbtc_context {
   int sm_count = 0;
   int* status_dev = nullptr;       // device status word (first recorded fault)
   long long wait_budget = 0;       // spins per bounded device wait (0 = default)
-  int tc_groups = 4;               // warpgroups per CTA of the tensor-core decode (3 or 4)
+  int tc_groups = 3;               // warpgroups per CTA of the tensor-core decode (3 or 4)
 };
 
 namespace nbtc {
@@ -32,7 +32,7 @@ nbtc_status make_level_views(const nbtc_latents* lat, int mip, LevelView* views)
 // Validates an MLP descriptor (shape and pointers).
 nbtc_status check_mlp(const nbtc_mlp* mlp);
 
-constexpr long long kDefaultWaitBudget = 1ll << 26;
+constexpr long long kDefaultWaitBudget = 1ll << 22;  // polls of up to 1 us: a few seconds
 
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 

@@ -96,10 +96,6 @@ struct TcWork {
   int reload;
 };
 
-constexpr int kMmaWarps = 4;       // one MMA-issuing warp per SM sub-partition
-
-
-
 constexpr int kSlots = 2;          // tile slots per warpgroup (ping-pong)
 constexpr int kStageBytes = 1024;  // per-warp output staging (32 texels x <= 16 halves)
 

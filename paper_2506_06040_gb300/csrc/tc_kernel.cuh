@@ -8,7 +8,7 @@
 //
 // Persistent, warp-specialised CTA (one per SM): W warpgroups of 128 threads
 // (one thread per tile row) compute features and run the epilogues, and
-// kMmaWarps warps issue the MMAs.  Each warpgroup owns two tile slots (TMEM
+// W warps (one per warpgroup) issue the MMAs.  Each warpgroup owns two tile slots (TMEM
 // columns + A buffers) and alternates between them, so one slot's SIMT work
 // overlaps the other slot's MMAs.  The CTA walks "chunks" -- runs of tiles of
 // one material -- and reloads the packed MLP only when the material changes.
@@ -27,9 +27,9 @@ using namespace sm100;
 
 // Tile numbering.  Each CTA owns a contiguous range of tile numbers; in
 // row-footprint mode consecutive numbers run down a column of 128-texel tiles
-// (number -> row = T % H, column block = T / H), so the tiles a CTA decodes at
-// the same time sit on neighbouring rows and share latent blocks in L1.
-// Returns the first output texel of tile T.
+// (number -> row = T % H, column block = T / H), so the consecutive tiles a
+// warpgroup decodes are consecutive rows of one column strip (the feature
+// stage's column cache relies on this).  Returns the first output texel of tile T.
 __device__ __forceinline__ int64_t tile_first_texel(const DecodeArgs& d, bool footprint, int64_t T) {
   if (!footprint) return T * 128;
   const uint32_t t = (uint32_t)T, h = (uint32_t)d.grid_h;
@@ -83,20 +83,25 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W) {
 }
 
 // Warp-specialised persistent kernel: W warpgroups (4 warps, one thread per
-// tile row) compute features and epilogues; warp 4W issues every MMA.  Each
-// warpgroup owns two tile slots (TMEM columns + A buffers) and alternates
-// between them, so one slot's epilogue runs while the other slot's MMAs run.
-// Slot q walks tiles q + NS * (blockIdx.x + gridDim.x * i).
+// tile row) compute features and epilogues; warp 4W + g issues the MMAs of
+// warpgroup g.  Each warpgroup owns two tile slots (TMEM columns + A buffers)
+// and alternates between them, so one slot's epilogue runs while the other
+// slot's MMAs run.  Inside a chunk, warpgroup g takes the g-th of W contiguous
+// tile ranges, its slots alternating over it.
 //
-// Hand-offs (all mbarriers, all waits bounded):
-//   A-ready[q]  (128 arrivals): slot q's A operand for its next layer is in smem
-//   D-ready[q]  (tcgen05.commit): that layer's accumulator is in TMEM
-// After a timeout a thread stops waiting but keeps its schedule (every
-// barrier and arrival still happens), so the kernel always terminates.
+// Hand-offs:
+//   A-ready[q]  named barrier (warpgroup: bar.arrive, its MMA warp: bar.sync,
+//               160 threads): slot q's A operand for its next layer is in smem
+//               and its previous accumulator has been read out of TMEM
+//   D-ready[q]  mbarrier (tcgen05.commit; bounded waits): that layer's
+//               accumulator is in TMEM
+// Every thread keeps its whole schedule whatever happens -- after a timed-out
+// wait it stops waiting but still makes every arrival -- so both barrier kinds
+// always complete and the kernel always terminates.
 // MODE kModeSingle: one material whose views are kernel parameters; kModeBatch:
 // chunks of many materials (and frame tiles) whose views live in shared memory.
 template <int NHID, bool FP8, int W, int MODE>
-__global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArgs p) {
+__global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   constexpr TcLayout L{NHID, FP8};
   constexpr int NS = W * kSlots;
   constexpr uint32_t kTmemCols = NS * kHid <= 256 ? 256 : 512;
@@ -107,7 +112,11 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
   const uint32_t sbase = smem_u32(smem);
   const int tid = threadIdx.x;
   const int warp = tid / 32, lane = tid % 32;
-  const uint32_t abar0 = sbase + S.bars, dbar0 = abar0 + NS * 8, wbar = dbar0 + NS * 8;
+  const uint32_t dbar0 = sbase + S.bars, wbar = dbar0 + NS * 8;
+  // named barriers: 0 = __syncthreads, 1 + g = warpgroup g's feature stage,
+  // 1 + W + q = A-ready of slot q
+  static_assert(1 + W + NS <= 16, "named barrier ids");
+  auto bar_a = [](int q) { return 1 + W + q; };
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S.tslot);
   TcWork& work = *reinterpret_cast<TcWork*>(smem + S.work);
   int* status = p.d.status;
@@ -117,10 +126,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int q = 0; q < NS; ++q) {
-      mbar_init(abar0 + q * 8, kTile);
-      mbar_init(dbar0 + q * 8, 1);
-    }
+    for (int q = 0; q < NS; ++q) mbar_init(dbar0 + q * 8, 1);
     mbar_init(wbar, 1);
     fence_mbar_init();
     work.m.packed = nullptr;
@@ -139,7 +145,6 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
   uint32_t wph = 0;  // phase of the weight barrier
 
   // slot state that lives across chunks (mbarrier phases)
-  uint32_t aph[kMmaWarps > 0 ? (NS + kMmaWarps - 1) / kMmaWarps : 1] = {};
   uint32_t dph[kSlots] = {};
   bool first_chunk = true;
 
@@ -192,11 +197,14 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
 
     if (warp >= 4 * W) {
       // ---------------------------------------------------------- MMA warps
-      // MMA warp m issues for slots q = m, m + kMmaWarps, ...  Descriptors are
-      // built once; per MMA only the 32-bit low word advances along K.
+      // MMA warp m serves warpgroup m's two slots.  The warpgroup hands its
+      // slots over in a fixed order (slot 0, slot 1, slot 0, ... while both
+      // have tiles), so the MMA warp takes them in that same order, blocked
+      // in the hardware barrier (no polling) until each is ready; lane 0
+      // issues.  Descriptors are built once; per MMA only the 32-bit low word
+      // advances along K.
       const int m = warp - 4 * W;
-      if (lane == 0 && m < NS) {
-        constexpr int NQ = (NS + kMmaWarps - 1) / kMmaWarps;
+      {
         constexpr uint32_t ID_HID = idesc(0, kTile, kHid);
         constexpr uint32_t ID_OUT = idesc(0, kTile, kOutPad);
         // high words: SBO, version, swizzle; low words: start address, LBO
@@ -206,95 +214,99 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
         auto lo = [](uint32_t addr, uint32_t lbo) { return (uint32_t)smem_desc(addr, lbo, 0, 0); };
         const uint32_t lo_w1 = lo(sbase + L.off_w1(), 128);
         const uint32_t lo_ones = lo(sbase + S.ones, 128);
-        int64_t next[NQ];
-        int stage[NQ];
+        const int64_t per_wg = (range_end + W - 1) / W;
+        const int64_t wg_end = min((int64_t)(m + 1) * per_wg, range_end);
+        int64_t next[kSlots];
+        int stage[kSlots];
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) {
-          next[i] = m + i * kMmaWarps;
-          stage[i] = 0;
+        for (int s = 0; s < kSlots; ++s) {
+          next[s] = (int64_t)m * per_wg + s;
+          stage[s] = 0;
         }
-        long long idle = 0;
         for (;;) {
-          bool any = false, progressed = false;
+          bool any = false;
 #pragma unroll
-          for (int i = 0; i < NQ; ++i) {
-            const int q = m + i * kMmaWarps;
-            if (q >= NS || next[i] >= range_end) continue;
+          for (int s = 0; s < kSlots; ++s) {
+            if (next[s] >= wg_end) continue;
             any = true;
-            if (!failed && !mbar_test_wait(abar0 + q * 8, aph[i])) continue;
-            aph[i] ^= 1u;
-            progressed = true;
-            tc_fence_after();
-            const uint32_t d = tmem_base + (uint32_t)(q * kHid);
-            const uint32_t slot = sbase + S.slots + q * S.slot;
-            const int l = stage[i];
-            if (l == 0) {
-              const uint64_t ad = ((uint64_t)hi_int << 32) | lo(slot + S.a0, 128);
-              const uint64_t bd = ((uint64_t)hi_int << 32) | lo_w1;
-              if constexpr (FP8) mma_f8(d, ad, bd, ID_HID, 0);
-              else mma_f16(d, ad, bd, ID_HID, 0);
-            } else {
-              const bool last = l == NHID;
-              const uint32_t id = last ? ID_OUT : ID_HID;
-              const uint32_t lo_a = lo(slot + S.ah, 16);
-              const uint32_t lo_b = lo(sbase + (last ? L.off_wo() : L.off_wh(l - 1)), 16);
-              if constexpr (FP8) {
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk)
-                  mma_f8(d, ((uint64_t)hi_w << 32) | (lo_a + 2 * kk), ((uint64_t)hi_w << 32) | (lo_b + 2 * kk), id,
-                         kk > 0);
+            const int q = m * kSlots + s;
+            named_bar_sync(bar_a(q), kTile + 32);
+            const int l = stage[s];
+            if (++stage[s] > NHID) {
+              stage[s] = 0;
+              next[s] += kSlots;
+            }
+            if (lane == 0) {
+              tc_fence_after();
+              const uint32_t d = tmem_base + (uint32_t)(q * kHid);
+              const uint32_t slot = sbase + S.slots + q * S.slot;
+              if (l == 0) {
+                const uint64_t ad = ((uint64_t)hi_int << 32) | lo(slot + S.a0, 128);
+                const uint64_t bd = ((uint64_t)hi_int << 32) | lo_w1;
+                if constexpr (FP8) mma_f8(d, ad, bd, ID_HID, 0);
+                else mma_f16(d, ad, bd, ID_HID, 0);
               } else {
-                const uint32_t lo_bt = lo(sbase + (last ? L.off_bto() : L.off_bth(l - 1)), 128);
-                mma_f16(d, ((uint64_t)hi_int << 32) | lo_ones, ((uint64_t)hi_int << 32) | lo_bt, id, 0);
+                const bool last = l == NHID;
+                const uint32_t id = last ? ID_OUT : ID_HID;
+                const uint32_t lo_a = lo(slot + S.ah, 16);
+                const uint32_t lo_b = lo(sbase + (last ? L.off_wo() : L.off_wh(l - 1)), 16);
+                if constexpr (FP8) {
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                  mma_f16(d, ((uint64_t)hi_w << 32) | (lo_a + 2 * kk), ((uint64_t)hi_w << 32) | (lo_b + 2 * kk), id,
-                          1);
+                  for (int kk = 0; kk < 2; ++kk)
+                    mma_f8(d, ((uint64_t)hi_w << 32) | (lo_a + 2 * kk), ((uint64_t)hi_w << 32) | (lo_b + 2 * kk), id,
+                           kk > 0);
+                } else {
+                  const uint32_t lo_bt = lo(sbase + (last ? L.off_bto() : L.off_bth(l - 1)), 128);
+                  mma_f16(d, ((uint64_t)hi_int << 32) | lo_ones, ((uint64_t)hi_int << 32) | lo_bt, id, 0);
+#pragma unroll
+                  for (int kk = 0; kk < 4; ++kk)
+                    mma_f16(d, ((uint64_t)hi_w << 32) | (lo_a + 2 * kk), ((uint64_t)hi_w << 32) | (lo_b + 2 * kk), id,
+                            1);
+                }
               }
+              mma_commit(dbar0 + q * 8);
             }
-            mma_commit(dbar0 + q * 8);
-            if (++stage[i] > NHID) {
-              stage[i] = 0;
-              next[i] += NS;
-            }
+            __syncwarp();  // converged before the next (aligned) barrier
           }
           if (!any) break;
-          if (progressed) {
-            idle = 0;
-          } else if (++idle > p.budget) {
-            failed = true;  // stop waiting; finish the schedule without waits
-            record_status(status, NBTC_ERR_TIMEOUT);
-          }
         }
       }
-      __syncwarp();
     } else {
       // ---------------------------------------------------------- warpgroups
       const int wg = warp / 4, wq = warp & 3;
       const int gt = tid % kTile;
       const int bar_id = 1 + wg;
       const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
-      unsigned char* stage_w = smem + S.stage + warp * kStageBytes;
+      const uint32_t stage_s = sbase + S.stage + warp * kStageBytes;
       const float* bias = reinterpret_cast<const float*>(smem + L.off_bias());
       const float* alpha = reinterpret_cast<const float*>(smem + L.off_alpha());
       const DecodeArgs& D = MODE == kModeSingle ? p.d : work.m.d;
       const int nout = work.m.nout;
+      // warpgroup wg decodes the contiguous tile range [wg_begin, wg_end) of the
+      // chunk, slot s taking tiles wg_begin + s, wg_begin + s + 2, ...; in
+      // row-footprint mode these are consecutive rows of one column strip
+      const int64_t per_wg = (range_end + W - 1) / W;
+      const int64_t wg_begin = min((int64_t)wg * per_wg, range_end);
+      const int64_t wg_end = min(wg_begin + per_wg, range_end);
+      StripCache cache;
+      strip_reset(cache);
       int64_t tile[kSlots];
       int stg[kSlots];
 
       // features of slot s's current tile -> A0, then A-ready
       auto start_tile = [&](int s) {
         const int q = wg * kSlots + s;
-        unsigned char* slot = smem + S.slots + q * S.slot;
         const uint32_t a0 = sbase + S.slots + q * S.slot + S.a0;
         float f[12];
         if (MODE == kModeSingle || grid_chunk) {
-          const int64_t t0 = tile_first_texel(D, footprint, work.c.first + tile[s]);
           if (footprint) {
-            // Ah is free: the previous tile's last MMA (which read it) has completed
-            footprint_features<kTile>(D, t0, gt, reinterpret_cast<float4*>(slot + S.ah), bar_id, f);
+            // tile T = column block T / H, row T % H; Ah is free: the previous
+            // tile's last MMA (which read it) has completed
+            const uint32_t T = (uint32_t)(work.c.first + tile[s]), H = (uint32_t)D.grid_h;
+            const uint32_t cb = T / H;
+            strip_features<kTile>(D, (int)(T - cb * H), (int)cb * kTile, gt, a0 - S.a0 + S.ah, bar_id, cache, f);
           } else {
-            const int64_t tex = t0 + gt;
+            const int64_t tex = (work.c.first + tile[s]) * kTile + gt;
             direct_features(D, tex < D.n ? tex : D.n - 1, f);
           }
         } else {
@@ -319,21 +331,22 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
           sts128(a0 + off_interleave(gt, 16), 0u, 0u, 0u, 0u);
         }
         fence_proxy_async_smem();
-        mbar_arrive(abar0 + q * 8);
+        __syncwarp();
+        named_bar_arrive(bar_a(q), kTile + 32);
         stg[s] = 0;
       };
 
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
-        tile[s] = wg * kSlots + s;
+        tile[s] = wg_begin + s;
         stg[s] = 0;
-        if (tile[s] < range_end) start_tile(s);
+        if (tile[s] < wg_end) start_tile(s);
       }
       for (;;) {
         bool any = false;
 #pragma unroll
         for (int s = 0; s < kSlots; ++s) {
-          if (tile[s] >= range_end) continue;
+          if (tile[s] >= wg_end) continue;
           any = true;
           const int q = wg * kSlots + s;
           if (!failed) failed = !mbar_wait_bounded(dbar0 + q * 8, dph[s], p.budget);
@@ -346,19 +359,24 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
             const uint32_t ah = sbase + S.slots + q * S.slot + S.ah;
             const float alp = alpha[stg[s]];
             const float* b = bias + stg[s] * kHid;
+            // the accumulator row comes out of TMEM in kParts loads, one wait each
+            // (one 64-column load would spill registers)
+            constexpr int kParts = 2;
+            constexpr int kPc = kHid / kParts;
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              uint32_t r[32];
+            for (int part = 0; part < kParts; ++part) {
+              uint32_t r[kPc];
               if (!failed) {
-                tmem_ld16(taddr + 32 * half, r);
-                tmem_ld16(taddr + 32 * half + 16, r + 16);
-                tmem_wait_ld32(r);
+#pragma unroll
+                for (int i = 0; i < kPc / 16; ++i) tmem_ld16(taddr + kPc * part + 16 * i, r + 16 * i);
+                if constexpr (kPc == 64) tmem_wait_ld64(r);
+                else tmem_wait_ld32(r);
               }
               if constexpr (!FP8) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < kPc / 8; ++c) {
                   const int j = 8 * c;
-                  sts128(ah + off_sw128(gt, 16 * (4 * half + c)),
+                  sts128(ah + off_sw128(gt, 16 * (part * (kPc / 8) + c)),
                          cvt_relu_f16x2(__uint_as_float(r[j + 0]), __uint_as_float(r[j + 1])),
                          cvt_relu_f16x2(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])),
                          cvt_relu_f16x2(__uint_as_float(r[j + 4]), __uint_as_float(r[j + 5])),
@@ -366,24 +384,25 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
                 }
               } else {
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
+                for (int c = 0; c < kPc / 16; ++c) {
                   uint32_t w[4];
 #pragma unroll
                   for (int e = 0; e < 4; ++e) {
-                    const int j = 16 * c + 4 * e, jj = 32 * half + j;
+                    const int j = 16 * c + 4 * e, jj = kPc * part + j;
                     w[e] = (uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j]), alp, b[jj]),
                                                      fmaf(__uint_as_float(r[j + 1]), alp, b[jj + 1])) |
                            ((uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j + 2]), alp, b[jj + 2]),
                                                       fmaf(__uint_as_float(r[j + 3]), alp, b[jj + 3]))
                             << 16);
                   }
-                  sts128(ah + off_sw64(gt, 16 * (2 * half + c)), w[0], w[1], w[2], w[3]);
+                  sts128(ah + off_sw64(gt, 16 * (part * (kPc / 16) + c)), w[0], w[1], w[2], w[3]);
                 }
               }
             }
             fence_proxy_async_smem();
             tc_fence_before();
-            mbar_arrive(abar0 + q * 8);
+            __syncwarp();
+            named_bar_arrive(bar_a(q), kTile + 32);
             ++stg[s];
           } else {
             // ---- output epilogue: accumulator -> FP16 -> global
@@ -403,17 +422,21 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
             if (MODE == kModeSingle || grid_chunk) {
               const int64_t t0 = tile_first_texel(D, footprint, work.c.first + tile[s]);
               const int64_t tex = t0 + gt;
-              if (t0 + kTile <= D.n) {  // per-warp coalesced: 32 texels x nout halves
-                uint16_t* st = reinterpret_cast<uint16_t*>(stage_w);
+              if (t0 + kTile <= D.n) {
+                // the warp's 32 texels x nout halves are contiguous in the output:
+                // stage them and write them with one bulk copy (64 nout bytes at a
+                // 64-byte multiple of the 16-byte aligned output)
+                if (lane == 0) bulk_wait_read0();  // the warp's previous bulk copy has read the stage
+                __syncwarp();
 #pragma unroll
                 for (int k = 0; k < kMaxOut; ++k)
-                  if (k < nout) st[lane * nout + k] = hv[k];
+                  if (k < nout) sts16(stage_s + 2u * (uint32_t)(lane * nout + k), hv[k]);
+                fence_proxy_async_smem();
                 __syncwarp();
-                const int n16 = 4 * nout;  // 32 texels x nout x 2 B / 16 B
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(D.out) + (t0 + 32 * wq) * nout);
-                const uint4* src = reinterpret_cast<const uint4*>(stage_w);
-                for (int c = lane; c < n16; c += 32) dst[c] = src[c];
-                __syncwarp();
+                if (lane == 0) {
+                  bulk_s2g(reinterpret_cast<uint16_t*>(D.out) + (t0 + 32 * wq) * nout, stage_s, 64u * (uint32_t)nout);
+                  bulk_commit();
+                }
               } else if (tex < D.n) {
                 uint16_t* o = reinterpret_cast<uint16_t*>(D.out) + tex * nout;
 #pragma unroll
@@ -429,8 +452,8 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
                   if (k < nout) o[k] = hv[k];
               }
             }
-            tile[s] += NS;
-            if (tile[s] < range_end) start_tile(s);
+            tile[s] += kSlots;
+            if (tile[s] < wg_end) start_tile(s);
           }
         }
         if (!any) break;
@@ -443,6 +466,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * kMmaWarps, 1) k_decode_tc(TcArg
     tc_fence_after();
   }
   if (failed && tid == 0) record_status(status, NBTC_ERR_TIMEOUT);
+  bulk_wait0();  // this thread's bulk output copies (if any) are complete
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -457,7 +481,7 @@ nbtc_status launch_tc_w(const TcArgs& p, int grid, cudaStream_t s) {
   nbtc_status st =
       cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S.total), "smem attribute");
   if (st) return st;
-  kern<<<grid, W * kTile + 32 * kMmaWarps, S.total, s>>>(p);
+  kern<<<grid, W * kTile + 32 * W, S.total, s>>>(p);
   return cuda_check(cudaGetLastError(), "launch k_decode_tc");
 }
 
