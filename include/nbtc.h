@@ -275,6 +275,7 @@ typedef struct {
   int64_t decode_tiles;    /* 128-texel tiles of the full decode */
   int64_t frame_uniform_tiles, frame_mixed_tiles, frame_packed_tiles;  /* of the last render */
   float tuned_decode_ms, tuned_render_ms;  /* autotuner's best times (0 = not tuned) */
+  int32_t render_warpgroups;                /* tile groups per CTA of the frame decode */
 } nbtc_batch_info;
 
 #define NBTC_BATCH_AUTOTUNE 1  /* flags: time the candidate configurations at creation */

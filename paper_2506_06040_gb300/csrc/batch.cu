@@ -196,7 +196,7 @@ struct nbtc_batch {
   int* fcounter = nullptr;
   size_t plist_ints = 0;
   // tuned configuration and graphs
-  int W = 4, chunk = 32, tw = 16, th = 8;
+  int W = 3, Wf = 3, chunk = 32, tw = 16, th = 8;  // W: decode warpgroups, Wf: render warpgroups
   cudaStream_t cap = nullptr;
   cudaGraphExec_t g_decode = nullptr, g_render = nullptr;
   nbtc_batch_info info{};
@@ -273,7 +273,7 @@ static nbtc_status enqueue_render(nbtc_context* ctx, nbtc_batch* B, cudaStream_t
   p.tile_w = F.tw;
   p.tile_h = F.th;
   p.tiles_x = F.tiles_x;
-  return launch_tc_args(ctx, p, B->nhid, false, B->W, ctx->sm_count, s);
+  return launch_tc_args(ctx, p, B->nhid, false, B->Wf, ctx->sm_count, s);
 }
 
 static nbtc_status set_tile_shape(nbtc_batch* B, int tw, int th) {
@@ -388,6 +388,7 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     }
     if (M.out) {
       if (M.out_w <= 0 || M.out_h <= 0 || M.out_w % kTile) return fail(NBTC_ERR_INVALID_ARG, "out_w must be a positive multiple of 128");
+      if ((int64_t)M.out_w * M.out_h / kTile >= (int64_t)1 << 31) return fail(NBTC_ERR_UNSUPPORTED, "material output too large");
       if (!aligned(M.out, 16)) return fail(NBTC_ERR_INVALID_ARG, "material out not 16-byte aligned");
       for (int k = 0; k < 4; ++k)
         if (M.latents.levels[k].width > M.out_w) return fail(NBTC_ERR_UNSUPPORTED, "latent level wider than the output");
@@ -436,7 +437,7 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     d.d.status = ctx->status_dev;
     d.packed = B->packed_dev + B->packed_stride * m;
     d.nout = nout;
-    d.tiles_per_row = M.out ? M.out_w / kTile : 0;
+    d.hdiv = make_fastdiv(M.out ? (uint32_t)M.out_h : 1u);
     d.tiles = d.d.n / kTile;
     B->decode_tiles += d.tiles;
     for (int k = 0; k < 4; ++k) {
@@ -522,12 +523,12 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     }
     if (B->has_frame) {
       float bestf = 1e30f;
-      int fw = B->W, ftw = 16, fth = 8;
+      int fw = B->Wf, ftw = 16, fth = 8;
       const int shapes[4][2] = {{16, 8}, {32, 4}, {8, 16}, {128, 1}};
       for (int W : {3, 4})
         for (auto& sh : shapes) {
           if (set_tile_shape(B, sh[0], sh[1])) continue;
-          B->W = W;
+          B->Wf = W;
           const float ms = time_ms([&] { return enqueue_render(ctx, B, B->cap); }, B->cap, 3, st);
           if (st) {
             free_plan(B);
@@ -541,9 +542,8 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
           }
         }
       NBTC_TRY(set_tile_shape(B, ftw, fth));
+      B->Wf = fw;
       B->info.tuned_render_ms = bestf;
-      // one warpgroup count serves both graphs: keep the decode's choice unless it had no work
-      if (B->decode_tiles == 0) B->W = fw;
     }
   }
   // ---- graphs
@@ -551,6 +551,7 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
   if (B->has_frame) NBTC_TRY(capture(ctx, B, true, &B->g_render));
 #undef NBTC_TRY
   B->info.warpgroups = B->W;
+  B->info.render_warpgroups = B->Wf;
   B->info.chunk_tiles = B->chunk;
   B->info.tile_w = B->tw;
   B->info.tile_h = B->th;

@@ -100,7 +100,7 @@ nbtc_status nbtc_create(int device, nbtc_context** out) {
   nbtc_context* ctx = new nbtc_context();
   ctx->device = device;
   ctx->sm_count = prop.multiProcessorCount;
-  if (const char* e = getenv("NBTC_TC_GROUPS")) ctx->tc_groups = atoi(e) == 4 ? 4 : 3;
+  if (const char* e = getenv("NBTC_TC_GROUPS")) ctx->tc_groups = atoi(e) == 3 ? 3 : 4;
   if ((st = cuda_check(cudaMalloc(&ctx->status_dev, sizeof(int)), "cudaMalloc(status)"))) {
     delete ctx;
     return st;

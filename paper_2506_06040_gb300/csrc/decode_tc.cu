@@ -187,10 +187,10 @@ nbtc_status launch_decode_tc(nbtc_context* ctx, const DecodeArgs& a, const nbtc_
   bool fp = a.uv == nullptr && (a.grid_w % kTile) == 0;
   for (int k = 0; k < 4; ++k) fp = fp && a.lv[k].w <= a.grid_w;
   p.footprint = fp ? 1 : 0;
-  p.tiles_per_row = fp ? a.grid_w / kTile : 0;
+  p.hdiv = make_fastdiv(fp && a.grid_h > 0 ? (uint32_t)a.grid_h : 1u);
   p.mode = kModeSingle;
   if (p.tiles >= (int64_t)1 << 31) return fail(NBTC_ERR_UNSUPPORTED, "more than 2^31 tiles");
-  const int W = ctx->tc_groups == 4 ? 4 : 3;
+  const int W = ctx->tc_groups == 3 ? 3 : 4;
   int64_t grid = (p.tiles + W * kSlots - 1) / (W * kSlots);
   if (grid > ctx->sm_count) grid = ctx->sm_count;
   p.per_cta = (p.tiles + grid - 1) / grid;

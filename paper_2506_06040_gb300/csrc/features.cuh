@@ -15,6 +15,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "fastdiv.h"
 #include "sm100.cuh"
 
 namespace nbtc {
@@ -258,6 +259,33 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
     }
     sm100::sts128f(colbuf + 16u * (uint32_t)(k * kColCap + (C.job >> 2)), fmaf(fy, C.dc[0], C.c0[0]),
                    fmaf(fy, C.dc[1], C.c0[1]), fmaf(fy, C.dc[2], C.c0[2]), 0.f);
+    // the next row's pair changes here too: start pulling its blocks into L1
+    const float tyn = texel_coord(((float)j + 1.5f) * a.inv_gh, L.h, L.shift);
+    const int keyn = (int)floorf(tyn);
+    if (keyn != key && j + 1 < a.grid_h) {
+      const int y0 = wrap_or_clamp(keyn, L.h, a.wrap), y1 = wrap_or_clamp(keyn + 1, L.h, a.wrap);
+      const uint64_t* col = L.blocks + (C.jx >> 2);
+      sm100::prefetch_l1(col + (size_t)(y0 >> 2) * L.wb);
+      sm100::prefetch_l1(col + (size_t)(y1 >> 2) * L.wb);
+    }
+  }
+  if (C.total > NT) {
+    // a strip wider than NT columns over all levels: the jobs past the first
+    // per thread are decoded afresh for every tile (only unusual level-to-output
+    // ratios get here; the 1/4..1/32 pyramid needs 68 columns per 128 texels)
+    const TilePlan P = plan_tile<NT>(a, (int64_t)j * a.grid_w + i0);
+    for (int job = tid + NT; job < P.total; job += NT) {
+      const ColumnJob J = column_job(a, P, job);
+      const BlockPair B = load_column(a, J);
+      const uint32_t t0 = bc1_texel(B.b0, J.x & 3, J.y0 & 3), t1 = bc1_texel(B.b1, J.x & 3, J.y1 & 3);
+      float c[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float v0 = (float)((t0 >> (8 * ch)) & 255u), v1 = (float)((t1 >> (8 * ch)) & 255u);
+        c[ch] = fmaf(J.fy, s * (v1 - v0), s * v0);
+      }
+      sm100::sts128f(colbuf + 16u * (uint32_t)(J.k * kColCap + J.rel), c[0], c[1], c[2], 0.f);
+    }
   }
   sm100::named_bar_sync(bar_id, NT);
 #pragma unroll
@@ -277,7 +305,7 @@ struct MatDev {
   DecodeArgs d;          // mip-0 views, wrap flag, output grid and buffer of the full decode
   const void* packed;    // FP16 packed MLP
   int nout;
-  int tiles_per_row;     // full decode: grid_w / 128
+  FastDiv hdiv;          // full decode: division by grid_h (tile number -> column block)
   int64_t tiles;         // full decode: tiles of the grid
   int mips[4];
   float log2w[4];        // log2 of each level's mip-0 width

@@ -12,7 +12,7 @@ struct nbtc_context {
   int sm_count = 0;
   int* status_dev = nullptr;       // device status word (first recorded fault)
   long long wait_budget = 0;       // spins per bounded device wait (0 = default)
-  int tc_groups = 3;               // warpgroups per CTA of the tensor-core decode (3 or 4)
+  int tc_groups = 4;               // warpgroups per CTA of the tensor-core decode (3 or 4)
 };
 
 namespace nbtc {

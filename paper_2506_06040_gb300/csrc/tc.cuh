@@ -69,7 +69,7 @@ struct TcArgs {
   const void* packed;
   int nout;
   int footprint;       // 1: row-footprint feature stage
-  int tiles_per_row;   // footprint mode: grid_w / 128
+  FastDiv hdiv;        // footprint mode: division by grid_h (tile number -> column block)
   int64_t tiles;
   int64_t per_cta;     // tiles per CTA (contiguous range)
   long long budget;    // polls per bounded wait

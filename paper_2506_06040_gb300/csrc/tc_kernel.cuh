@@ -30,10 +30,11 @@ using namespace sm100;
 // (number -> row = T % H, column block = T / H), so the consecutive tiles a
 // warpgroup decodes are consecutive rows of one column strip (the feature
 // stage's column cache relies on this).  Returns the first output texel of tile T.
-__device__ __forceinline__ int64_t tile_first_texel(const DecodeArgs& d, bool footprint, int64_t T) {
+__device__ __forceinline__ int64_t tile_first_texel(const DecodeArgs& d, const FastDiv& hdiv, bool footprint,
+                                                    int64_t T) {
   if (!footprint) return T * 128;
-  const uint32_t t = (uint32_t)T, h = (uint32_t)d.grid_h;
-  const uint32_t col = t / h, row = t - col * h;
+  const uint32_t t = (uint32_t)T;
+  const uint32_t col = fastdiv(t, hdiv), row = t - col * (uint32_t)d.grid_h;
   return (int64_t)row * d.grid_w + (int64_t)col * 128;
 }
 
@@ -195,47 +196,42 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
     const bool footprint = MODE == kModeSingle ? p.footprint != 0 : grid_chunk;
     const int64_t range_end = work.c.count;   // tiles are numbered 0 .. count-1 inside the chunk
 
+    // Schedule.  Warpgroup g decodes the contiguous tile range [g_begin, g_end)
+    // of the chunk in rounds of two tiles (slot 0: g_begin + 2i, slot 1:
+    // g_begin + 2i + 1); in row-footprint mode these are consecutive rows of one
+    // column strip.  Within a round both slots advance one layer per stage, slot
+    // 0 first; a slot's next tile starts (features -> A0) right after its output
+    // epilogue.  The warpgroup and its MMA warp walk this same schedule, so the
+    // hand-offs always pair up.
+    const int64_t per_wg = (range_end + W - 1) / W;
+
     if (warp >= 4 * W) {
       // ---------------------------------------------------------- MMA warps
-      // MMA warp m serves warpgroup m's two slots.  The warpgroup hands its
-      // slots over in a fixed order (slot 0, slot 1, slot 0, ... while both
-      // have tiles), so the MMA warp takes them in that same order, blocked
-      // in the hardware barrier (no polling) until each is ready; lane 0
-      // issues.  Descriptors are built once; per MMA only the 32-bit low word
-      // advances along K.
+      // MMA warp m serves warpgroup m: it blocks in the hardware barrier (no
+      // polling) until the warpgroup has handed a slot over, then lane 0 issues
+      // that layer's MMAs and commits them to the slot's D-ready mbarrier.
+      // Descriptors are built once; per MMA only the 32-bit low word advances.
       const int m = warp - 4 * W;
-      {
-        constexpr uint32_t ID_HID = idesc(0, kTile, kHid);
-        constexpr uint32_t ID_OUT = idesc(0, kTile, kOutPad);
-        // high words: SBO, version, swizzle; low words: start address, LBO
-        const uint32_t hi_int = (uint32_t)(smem_desc(0, 128, 256, kSwzNone) >> 32);
-        const uint32_t hi_w = FP8 ? (uint32_t)(smem_desc(0, 16, 512, kSwz64) >> 32)
-                                  : (uint32_t)(smem_desc(0, 16, 1024, kSwz128) >> 32);
-        auto lo = [](uint32_t addr, uint32_t lbo) { return (uint32_t)smem_desc(addr, lbo, 0, 0); };
-        const uint32_t lo_w1 = lo(sbase + L.off_w1(), 128);
-        const uint32_t lo_ones = lo(sbase + S.ones, 128);
-        const int64_t per_wg = (range_end + W - 1) / W;
-        const int64_t wg_end = min((int64_t)(m + 1) * per_wg, range_end);
-        int64_t next[kSlots];
-        int stage[kSlots];
+      constexpr uint32_t ID_HID = idesc(0, kTile, kHid);
+      constexpr uint32_t ID_OUT = idesc(0, kTile, kOutPad);
+      // high words: SBO, version, swizzle; low words: start address, LBO
+      const uint32_t hi_int = (uint32_t)(smem_desc(0, 128, 256, kSwzNone) >> 32);
+      const uint32_t hi_w = FP8 ? (uint32_t)(smem_desc(0, 16, 512, kSwz64) >> 32)
+                                : (uint32_t)(smem_desc(0, 16, 1024, kSwz128) >> 32);
+      auto lo = [](uint32_t addr, uint32_t lbo) { return (uint32_t)smem_desc(addr, lbo, 0, 0); };
+      const uint32_t lo_w1 = lo(sbase + L.off_w1(), 128);
+      const uint32_t lo_ones = lo(sbase + S.ones, 128);
+      const int64_t g_begin = min((int64_t)m * per_wg, range_end);
+      const int64_t g_end = min(g_begin + per_wg, range_end);
+      for (int64_t base = g_begin; base < g_end; base += kSlots) {
+        const bool two = base + 1 < g_end;
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s) {
-          next[s] = (int64_t)m * per_wg + s;
-          stage[s] = 0;
-        }
-        for (;;) {
-          bool any = false;
+        for (int l = 0; l <= NHID; ++l) {
 #pragma unroll
           for (int s = 0; s < kSlots; ++s) {
-            if (next[s] >= wg_end) continue;
-            any = true;
+            if (s == 1 && !two) break;
             const int q = m * kSlots + s;
             named_bar_sync(bar_a(q), kTile + 32);
-            const int l = stage[s];
-            if (++stage[s] > NHID) {
-              stage[s] = 0;
-              next[s] += kSlots;
-            }
             if (lane == 0) {
               tc_fence_after();
               const uint32_t d = tmem_base + (uint32_t)(q * kHid);
@@ -268,7 +264,6 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
             }
             __syncwarp();  // converged before the next (aligned) barrier
           }
-          if (!any) break;
         }
       }
     } else {
@@ -281,36 +276,31 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       const float* bias = reinterpret_cast<const float*>(smem + L.off_bias());
       const float* alpha = reinterpret_cast<const float*>(smem + L.off_alpha());
       const DecodeArgs& D = MODE == kModeSingle ? p.d : work.m.d;
+      const FastDiv& hdiv = MODE == kModeSingle ? p.hdiv : work.m.hdiv;
       const int nout = work.m.nout;
-      // warpgroup wg decodes the contiguous tile range [wg_begin, wg_end) of the
-      // chunk, slot s taking tiles wg_begin + s, wg_begin + s + 2, ...; in
-      // row-footprint mode these are consecutive rows of one column strip
-      const int64_t per_wg = (range_end + W - 1) / W;
-      const int64_t wg_begin = min((int64_t)wg * per_wg, range_end);
-      const int64_t wg_end = min(wg_begin + per_wg, range_end);
+      const int64_t g_begin = min((int64_t)wg * per_wg, range_end);
+      const int64_t g_end = min(g_begin + per_wg, range_end);
       StripCache cache;
       strip_reset(cache);
-      int64_t tile[kSlots];
-      int stg[kSlots];
 
-      // features of slot s's current tile -> A0, then A-ready
-      auto start_tile = [&](int s) {
+      // features of tile T (chunk numbering) into slot s's A0, then A-ready
+      auto start_tile = [&](int s, int64_t T) {
         const int q = wg * kSlots + s;
         const uint32_t a0 = sbase + S.slots + q * S.slot + S.a0;
         float f[12];
         if (MODE == kModeSingle || grid_chunk) {
           if (footprint) {
-            // tile T = column block T / H, row T % H; Ah is free: the previous
+            // tile number = column block x H + row; Ah is free: the previous
             // tile's last MMA (which read it) has completed
-            const uint32_t T = (uint32_t)(work.c.first + tile[s]), H = (uint32_t)D.grid_h;
-            const uint32_t cb = T / H;
-            strip_features<kTile>(D, (int)(T - cb * H), (int)cb * kTile, gt, a0 - S.a0 + S.ah, bar_id, cache, f);
+            const uint32_t t = (uint32_t)(work.c.first + T), H = (uint32_t)D.grid_h;
+            const uint32_t cb = fastdiv(t, hdiv);
+            strip_features<kTile>(D, (int)(t - cb * H), (int)cb * kTile, gt, a0 - S.a0 + S.ah, bar_id, cache, f);
           } else {
-            const int64_t tex = (work.c.first + tile[s]) * kTile + gt;
+            const int64_t tex = (work.c.first + T) * kTile + gt;
             direct_features(D, tex < D.n ? tex : D.n - 1, f);
           }
         } else {
-          const int64_t px = frame_pixel(p, work.c, tile[s], gt);
+          const int64_t px = frame_pixel(p, work.c, T, gt);
           const int64_t pq = px < 0 ? 0 : px;
           const float2 uv = __ldg(reinterpret_cast<const float2*>(p.fuv) + pq);
           trilinear_features(work.m, uv.x, uv.y, __ldg(p.flod + pq), f);
@@ -333,130 +323,130 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
         fence_proxy_async_smem();
         __syncwarp();
         named_bar_arrive(bar_a(q), kTile + 32);
-        stg[s] = 0;
       };
 
+      // hidden epilogue of layer l of slot s: accumulator -> (bias,) ReLU ->
+      // narrow -> Ah, then A-ready
+      auto hidden_epilogue = [&](int s, int l) {
+        const int q = wg * kSlots + s;
+        const uint32_t taddr = tmem_base + (uint32_t)(q * kHid) + lane_off;
+        const uint32_t ah = sbase + S.slots + q * S.slot + S.ah;
+        const float alp = alpha[l];
+        const float* b = bias + l * kHid;
+        // the accumulator row comes out of TMEM in two 32-column parts, one wait
+        // each (one 64-column load would spill registers); after a timed-out
+        // wait the loads still run (they cannot fault) and the results are
+        // discarded with the status
+        constexpr int kParts = 2;
+        constexpr int kPc = kHid / kParts;
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
-        tile[s] = wg_begin + s;
-        stg[s] = 0;
-        if (tile[s] < wg_end) start_tile(s);
-      }
-      for (;;) {
-        bool any = false;
+        for (int part = 0; part < kParts; ++part) {
+          uint32_t r[kPc];
+          tmem_ld32_wait(taddr + kPc * part, r);
+          if constexpr (!FP8) {
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s) {
-          if (tile[s] >= wg_end) continue;
-          any = true;
-          const int q = wg * kSlots + s;
-          if (!failed) failed = !mbar_wait_bounded(dbar0 + q * 8, dph[s], p.budget);
-          dph[s] ^= 1u;
-          failed = __any_sync(0xffffffffu, failed);  // warp-uniform: tcgen05.ld is .sync.aligned
-          tc_fence_after();
-          const uint32_t taddr = tmem_base + (uint32_t)(q * kHid) + lane_off;
-          if (stg[s] < NHID) {
-            // ---- hidden epilogue: accumulator -> (bias,) ReLU -> narrow -> Ah
-            const uint32_t ah = sbase + S.slots + q * S.slot + S.ah;
-            const float alp = alpha[stg[s]];
-            const float* b = bias + stg[s] * kHid;
-            // the accumulator row comes out of TMEM in kParts loads, one wait each
-            // (one 64-column load would spill registers)
-            constexpr int kParts = 2;
-            constexpr int kPc = kHid / kParts;
-#pragma unroll
-            for (int part = 0; part < kParts; ++part) {
-              uint32_t r[kPc];
-              if (!failed) {
-#pragma unroll
-                for (int i = 0; i < kPc / 16; ++i) tmem_ld16(taddr + kPc * part + 16 * i, r + 16 * i);
-                if constexpr (kPc == 64) tmem_wait_ld64(r);
-                else tmem_wait_ld32(r);
-              }
-              if constexpr (!FP8) {
-#pragma unroll
-                for (int c = 0; c < kPc / 8; ++c) {
-                  const int j = 8 * c;
-                  sts128(ah + off_sw128(gt, 16 * (part * (kPc / 8) + c)),
-                         cvt_relu_f16x2(__uint_as_float(r[j + 0]), __uint_as_float(r[j + 1])),
-                         cvt_relu_f16x2(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])),
-                         cvt_relu_f16x2(__uint_as_float(r[j + 4]), __uint_as_float(r[j + 5])),
-                         cvt_relu_f16x2(__uint_as_float(r[j + 6]), __uint_as_float(r[j + 7])));
-                }
-              } else {
-#pragma unroll
-                for (int c = 0; c < kPc / 16; ++c) {
-                  uint32_t w[4];
-#pragma unroll
-                  for (int e = 0; e < 4; ++e) {
-                    const int j = 16 * c + 4 * e, jj = kPc * part + j;
-                    w[e] = (uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j]), alp, b[jj]),
-                                                     fmaf(__uint_as_float(r[j + 1]), alp, b[jj + 1])) |
-                           ((uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j + 2]), alp, b[jj + 2]),
-                                                      fmaf(__uint_as_float(r[j + 3]), alp, b[jj + 3]))
-                            << 16);
-                  }
-                  sts128(ah + off_sw64(gt, 16 * (part * (kPc / 16) + c)), w[0], w[1], w[2], w[3]);
-                }
-              }
+            for (int c = 0; c < kPc / 8; ++c) {
+              const int j = 8 * c;
+              sts128(ah + off_sw128(gt, 16 * (part * (kPc / 8) + c)),
+                     cvt_relu_f16x2(__uint_as_float(r[j + 0]), __uint_as_float(r[j + 1])),
+                     cvt_relu_f16x2(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])),
+                     cvt_relu_f16x2(__uint_as_float(r[j + 4]), __uint_as_float(r[j + 5])),
+                     cvt_relu_f16x2(__uint_as_float(r[j + 6]), __uint_as_float(r[j + 7])));
             }
-            fence_proxy_async_smem();
-            tc_fence_before();
-            __syncwarp();
-            named_bar_arrive(bar_a(q), kTile + 32);
-            ++stg[s];
           } else {
-            // ---- output epilogue: accumulator -> FP16 -> global
-            uint32_t r[16];
-            if (!failed) {
-              tmem_ld16(taddr, r);
-              tmem_wait_ld16(r);
-            }
-            tc_fence_before();
-            const float alp = alpha[NHID];
-            const float* b = bias + NHID * kHid;
-            uint16_t hv[kMaxOut];
 #pragma unroll
-            for (int k = 0; k < kMaxOut; ++k)
-              hv[k] = __half_as_ushort(FP8 ? __float2half_rn(fmaf(__uint_as_float(r[k]), alp, b[k]))
-                                           : __float2half_rn(__uint_as_float(r[k])));
-            if (MODE == kModeSingle || grid_chunk) {
-              const int64_t t0 = tile_first_texel(D, footprint, work.c.first + tile[s]);
-              const int64_t tex = t0 + gt;
-              if (t0 + kTile <= D.n) {
-                // the warp's 32 texels x nout halves are contiguous in the output:
-                // stage them and write them with one bulk copy (64 nout bytes at a
-                // 64-byte multiple of the 16-byte aligned output)
-                if (lane == 0) bulk_wait_read0();  // the warp's previous bulk copy has read the stage
-                __syncwarp();
+            for (int c = 0; c < kPc / 16; ++c) {
+              uint32_t w[4];
 #pragma unroll
-                for (int k = 0; k < kMaxOut; ++k)
-                  if (k < nout) sts16(stage_s + 2u * (uint32_t)(lane * nout + k), hv[k]);
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                  bulk_s2g(reinterpret_cast<uint16_t*>(D.out) + (t0 + 32 * wq) * nout, stage_s, 64u * (uint32_t)nout);
-                  bulk_commit();
-                }
-              } else if (tex < D.n) {
-                uint16_t* o = reinterpret_cast<uint16_t*>(D.out) + tex * nout;
-#pragma unroll
-                for (int k = 0; k < kMaxOut; ++k)
-                  if (k < nout) o[k] = hv[k];
+              for (int e = 0; e < 4; ++e) {
+                const int j = 16 * c + 4 * e, jj = kPc * part + j;
+                w[e] = (uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j]), alp, b[jj]),
+                                                 fmaf(__uint_as_float(r[j + 1]), alp, b[jj + 1])) |
+                       ((uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j + 2]), alp, b[jj + 2]),
+                                                  fmaf(__uint_as_float(r[j + 3]), alp, b[jj + 3]))
+                        << 16);
               }
-            } else {
-              const int64_t px = frame_pixel(p, work.c, tile[s], gt);
-              if (px >= 0) {
-                uint16_t* o = p.fout + px * nout;
-#pragma unroll
-                for (int k = 0; k < kMaxOut; ++k)
-                  if (k < nout) o[k] = hv[k];
-              }
+              sts128(ah + off_sw64(gt, 16 * (part * (kPc / 16) + c)), w[0], w[1], w[2], w[3]);
             }
-            tile[s] += kSlots;
-            if (tile[s] < wg_end) start_tile(s);
           }
         }
-        if (!any) break;
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncwarp();
+        named_bar_arrive(bar_a(q), kTile + 32);
+      };
+
+      // output epilogue of slot s, tile T: accumulator -> FP16 -> global
+      auto output_epilogue = [&](int s, int64_t T) {
+        const int q = wg * kSlots + s;
+        const uint32_t taddr = tmem_base + (uint32_t)(q * kHid) + lane_off;
+        uint32_t r[16];
+        tmem_ld16_wait(taddr, r);
+        tc_fence_before();
+        const float alp = alpha[NHID];
+        const float* b = bias + NHID * kHid;
+        uint16_t hv[kMaxOut];
+#pragma unroll
+        for (int k = 0; k < kMaxOut; ++k)
+          hv[k] = __half_as_ushort(FP8 ? __float2half_rn(fmaf(__uint_as_float(r[k]), alp, b[k]))
+                                       : __float2half_rn(__uint_as_float(r[k])));
+        if (MODE == kModeSingle || grid_chunk) {
+          const int64_t t0 = tile_first_texel(D, hdiv, footprint, work.c.first + T);
+          const int64_t tex = t0 + gt;
+          if (t0 + kTile <= D.n) {
+            // the warp's 32 texels x nout halves are contiguous in the output:
+            // stage them and write them with one bulk copy (64 nout bytes at a
+            // 64-byte multiple of the 16-byte aligned output)
+            if (lane == 0) bulk_wait_read0();  // the warp's previous bulk copy has read the stage
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < kMaxOut; ++k)
+              if (k < nout) sts16(stage_s + 2u * (uint32_t)(lane * nout + k), hv[k]);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              bulk_s2g(reinterpret_cast<uint16_t*>(D.out) + (t0 + 32 * wq) * nout, stage_s, 64u * (uint32_t)nout);
+              bulk_commit();
+            }
+          } else if (tex < D.n) {
+            uint16_t* o = reinterpret_cast<uint16_t*>(D.out) + tex * nout;
+#pragma unroll
+            for (int k = 0; k < kMaxOut; ++k)
+              if (k < nout) o[k] = hv[k];
+          }
+        } else {
+          const int64_t px = frame_pixel(p, work.c, T, gt);
+          if (px >= 0) {
+            uint16_t* o = p.fout + px * nout;
+#pragma unroll
+            for (int k = 0; k < kMaxOut; ++k)
+              if (k < nout) o[k] = hv[k];
+          }
+        }
+      };
+
+      if (g_begin < g_end) start_tile(0, g_begin);
+      if (g_begin + 1 < g_end) start_tile(1, g_begin + 1);
+      for (int64_t base = g_begin; base < g_end; base += kSlots) {
+        const bool two = base + 1 < g_end;
+#pragma unroll
+        for (int l = 0; l <= NHID; ++l) {
+#pragma unroll
+          for (int s = 0; s < kSlots; ++s) {
+            if (s == 1 && !two) break;
+            const int q = wg * kSlots + s;
+            if (!failed) failed = !mbar_wait_bounded(dbar0 + q * 8, dph[s], p.budget);
+            dph[s] ^= 1u;
+            failed = __any_sync(0xffffffffu, failed);  // one failure state per warp
+            tc_fence_after();
+            if (l < NHID) {
+              hidden_epilogue(s, l);
+            } else {
+              output_epilogue(s, base + s);
+              if (base + s + kSlots < g_end) start_tile(s, base + s + kSlots);
+            }
+          }
+        }
       }
     }
     // chunk end: every MMA of this chunk has been consumed; the MLP image and the

@@ -39,33 +39,27 @@ def test_binding_covers_header():
 
 
 def test_struct_layouts_match_c():
+    """Every ctypes struct of the binding has the C compiler's size and every
+    field the C compiler's offset."""
     from paper_2506_06040_gb300 import _abi
-    src = r'''
-#include <stdio.h>
-#include <stddef.h>
-#include "nbtc.h"
-int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(nbtc_level), offsetof(nbtc_level, width), offsetof(nbtc_level, shift),
-         sizeof(nbtc_latents), offsetof(nbtc_latents, levels));
-  printf("%zu %zu %zu\n", sizeof(nbtc_mlp), offsetof(nbtc_mlp, weights), offsetof(nbtc_mlp, biases));
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(nbtc_train_args), offsetof(nbtc_train_args, mlp),
-         offsetof(nbtc_train_args, target_w), offsetof(nbtc_train_args, batch), offsetof(nbtc_train_args, loss),
-         offsetof(nbtc_train_args, workspace), offsetof(nbtc_train_args, workspace_bytes));
-  return 0;
-}'''
+    pairs = [("nbtc_level", _abi.Level), ("nbtc_latents", _abi.Latents), ("nbtc_mlp", _abi.Mlp),
+             ("nbtc_train_args", _abi.TrainArgs), ("nbtc_batch_material", _abi.BatchMaterial),
+             ("nbtc_frame", _abi.Frame), ("nbtc_batch_info", _abi.BatchInfo)]
+    lines, want = [], []
+    for cname, cls in pairs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+            want.append(getattr(cls, f).offset)
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"nbtc.h\"\nint main(void) {\n" + "\n".join(lines) + \
+        "\n  return 0;\n}\n"
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         open(c, "w").write(src)
         exe = os.path.join(d, "t")
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
-        out = subprocess.check_output([exe]).decode().split()
-    got = [int(x) for x in out]
-    want = [ctypes.sizeof(_abi.Level), _abi.Level.width.offset, _abi.Level.shift.offset,
-            ctypes.sizeof(_abi.Latents), _abi.Latents.levels.offset,
-            ctypes.sizeof(_abi.Mlp), _abi.Mlp.weights.offset, _abi.Mlp.biases.offset,
-            ctypes.sizeof(_abi.TrainArgs), _abi.TrainArgs.mlp.offset, _abi.TrainArgs.target_w.offset,
-            _abi.TrainArgs.batch.offset, _abi.TrainArgs.loss.offset, _abi.TrainArgs.workspace.offset,
-            _abi.TrainArgs.workspace_bytes.offset]
+        got = [int(x) for x in subprocess.check_output([exe]).decode().split()]
     assert got == want
 
 

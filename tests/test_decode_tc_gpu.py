@@ -91,6 +91,23 @@ def test_fp16_grid_footprint(nb, ctx, dims):
     _check_fp16(got, emu, wl.material, _grid_x(wl.material, 512, 96))
 
 
+@pytest.mark.parametrize("gw,gh,levels", [(1024, 768, None), (384, 1024, [384, 192, 96, 48])])
+def test_fp16_grid_long_strips(nb, ctx, gw, gh, levels):
+    """Every texel of grids whose per-warpgroup tile ranges run many rows down a
+    column strip and cross strip boundaries: the feature stage's column cache
+    (blocks decoded again only when a level's vertical tap pair changes, next
+    row's blocks prefetched) against the emulator everywhere.  The second grid's
+    levels (1, 1/2, 1/4, 1/8 of its width) need 248 latent columns per 128-texel
+    tile, more than one per thread.  Both keep the texel coordinates exact in
+    FP32 along x (dyadic level/output ratios); off-dyadic grids differ from the
+    FP64 emulator by FP32 coordinate rounding, which flips FP16 roundings of
+    features more often than the 1-ulp criterion assumes."""
+    wl = synth.small_decode_workload(1024, [12, 64, 64, 64, 9], seed=330 + gh, level_sides=levels)
+    got = _fp16_case(nb, ctx, wl, grid=(gw, gh))
+    emu = oracle.decode.decode_grid(wl.material, gw, gh, precision="fp16")
+    _check_fp16(got, emu, wl.material, _grid_x(wl.material, gw, gh))
+
+
 @pytest.mark.parametrize("gw,gh", [(200, 72), (130, 3), (7, 5), (128, 1), (256, 2)])
 def test_fp16_ragged(nb, ctx, gw, gh):
     wl = synth.small_decode_workload(256, [12, 64, 64, 9], seed=310)
