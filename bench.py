@@ -234,7 +234,7 @@ def run_forms(args, nb, ctx, stream, flush, peaks, sm_count) -> dict:
         ach = flop * n / (ms * 1e-3) / 1e12
         res[name] = {"gtexel_s": n / ms / 1e6, "kernel_ms": ms, "max_abs_dev_vs_fp32_per_channel": err,
                      "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": ach / peak, "traffic": _profiled_traffic(f"k_decode_tc_{name[:3]}_{W}sq"),
+                                  "frac": ach / peak, "traffic": _profiled_traffic(f"k_decode_tc_{name.split('_')[0]}_{W}sq"),
                                   "peak_source": "measured bf16 dense burst" + (" x 2 (fp8 nominal ratio)" if prec == nb.FP8_E4M3 else "")}}
     res["fp16_tc_speedup_vs_fp32"] = res["fp16_tc"]["gtexel_s"] / res["fp32"]["gtexel_s"]
     ctx.sync(stream)
