@@ -259,11 +259,27 @@ def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
     flop = 32640 * wl.batch
     peak = _fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
     ctx.sync(stream)
-    return {"workload": wl.name, "steps_per_s": 1e3 / ms, "samples_per_s": wl.batch * 1e3 / ms, "ms_per_step": ms,
-            "kernels_per_step": 6,
-            "roofline": {"bound": "alu", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": flop / (ms * 1e-3) / 1e12 / peak,
-                         "note": "whole step (forward, backward, reduction, Adam) against the FP32 FFMA peak"}}
+    res = {"workload": wl.name, "steps_per_s": 1e3 / ms, "samples_per_s": wl.batch * 1e3 / ms, "ms_per_step": ms,
+           "kernels_per_step": 6,
+           "roofline": {"bound": "alu", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": flop / (ms * 1e-3) / 1e12 / peak,
+                        "note": "whole step (forward, backward, reduction, Adam) against the FP32 FFMA peak"}}
+    # the same step on quantisation-aware BC1 latents (raw endpoints + blend factors
+    # per level, N(0, 1)): decode, step, straight-through backward, Adam on the raw
+    # parameters
+    from paper_2506_06040_gb300.train import QatModel
+    rng = synth.Rng(1003, 9)
+    e0 = [rng.normal(s * s // 16 * 3, 1.0).reshape(s // 4, s // 4, 3) for s in wl.latent_sides]
+    e1 = [rng.normal(s * s // 16 * 3, 1.0).reshape(s // 4, s // 4, 3) for s in wl.latent_sides]
+    al = [rng.normal(s * s, 1.0).reshape(s, s) for s in wl.latent_sides]
+    qm = QatModel(e0, e1, al, wl.shifts, wl.mlp.weights, wl.mlp.biases)
+    tq = _time_steps(lambda: qm.train_step(ctx, uvs[next(it) % 4], tgt, stream=stream),
+                     max(3, args.steps // 2), args.warmup, flush, stream)
+    msq = statistics.mean(tq)
+    ctx.sync(stream)
+    res["qat"] = {"steps_per_s": 1e3 / msq, "samples_per_s": wl.batch * 1e3 / msq, "ms_per_step": msq,
+                  "kernels_per_step": 6 + 4 + 4 * 4}
+    return res
 
 
 def run_batch(args, nb, ctx, stream, flush) -> dict:

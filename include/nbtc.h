@@ -231,6 +231,49 @@ nbtc_status nbtc_forward_continuous(nbtc_context* ctx, const nbtc_train_args* ar
 nbtc_status nbtc_backward_continuous(nbtc_context* ctx, const nbtc_train_args* args, const float* dy_dev,
                                      void* stream);
 
+/* ------------------------------------------------------------------ QAT BC1 latents
+ *
+ * Quantisation-aware training of the BC1 latents themselves (Sec. 3.2,
+ * Eqs. 1-3): a level is held as raw FP32 parameters -- per 4x4 block two
+ * endpoints e0, e1 (RGB), per texel a blend factor alpha -- and decodes to
+ * T = (1 - a) E0 + a E1 with a = quant(sigmoid(alpha), 2 bits) and
+ * E = quant(sigmoid(e), [5, 6, 5] bits); quant picks the nearest of the 2^b
+ * levels k / (2^b - 1), decided as the number of FP32 thresholds
+ * logit((j + 1/2) / (2^b - 1)) that the raw FP32 parameter reaches (no exp in
+ * the decision).  The backward passes the quantisers' gradient straight through,
+ * so dL/dalpha = sum_c dL/dT_c (E1_c - E0_c) s'(alpha) and dL/de0 = sum over the
+ * block's texels of dL/dT (1 - a) s'(e0) (likewise e1 with a), s' = s (1 - s).
+ * The encoder turns the parameters into real BC1 blocks: endpoint codes
+ * R << 11 | G << 5 | B, level q of alpha mapped to palette index 0 (q = 0),
+ * 2 (q = 1), 3 (q = 2), 1 (q = 3) in four-colour mode; endpoints swapped (and
+ * q -> 3 - q) when code(e0) < code(e1); every index 0 when the codes are equal.
+ * All arrays are device FP32, caller-owned, row-major. */
+typedef struct {
+  int32_t width, height;                   /* texels, positive multiples of 4 */
+  float* e0; float* e1;                     /* [height/4][width/4][3] raw endpoints */
+  float* alpha;                             /* [height][width] raw blend factors */
+  float* g_e0; float* g_e1; float* g_alpha; /* gradients (written by the step) */
+  float* m_e0; float* v_e0;                 /* Adam moments (step only) */
+  float* m_e1; float* v_e1;
+  float* m_alpha; float* v_alpha;
+} nbtc_qat_level;
+
+/* Decoded texture of one QAT level: out [height][width][3] FP32. */
+nbtc_status nbtc_qat_decode(nbtc_context* ctx, const nbtc_qat_level* level, float* out, void* stream);
+
+/* BC1 blocks of one QAT level: blocks [height/4][width/4] (uint64). */
+nbtc_status nbtc_qat_encode(nbtc_context* ctx, const nbtc_qat_level* level, uint64_t* blocks, void* stream);
+
+/* One QAT training step: decodes the 4 levels into args->latents (caller-owned
+ * scratch of the decoded textures, sizes args->widths / heights, which must
+ * equal the levels'), runs the training step of nbtc_train_step on them
+ * (forward, loss, backward, MLP Adam; args->latent_grads receives dL/dT,
+ * args->latent_m / latent_v are not used), carries dL/dT to the raw parameters
+ * straight through the quantisers (g_e0, g_e1, g_alpha) and updates them with
+ * Adam at args->lr_latent. */
+nbtc_status nbtc_train_step_qat(nbtc_context* ctx, const nbtc_train_args* args, const nbtc_qat_level* levels,
+                                float* loss_dev, void* stream);
+
 /* ------------------------------------------------------------------ batching
  *
  * Many materials, each with its own BC1 pyramid (with mips) and its own MLP,

@@ -45,6 +45,13 @@ class TrainArgs(ctypes.Structure):
                 ("workspace_bytes", c_size_t)]
 
 
+class QatLevel(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("e0", c_void_p), ("e1", c_void_p), ("alpha", c_void_p),
+                ("g_e0", c_void_p), ("g_e1", c_void_p), ("g_alpha", c_void_p), ("m_e0", c_void_p),
+                ("v_e0", c_void_p), ("m_e1", c_void_p), ("v_e1", c_void_p), ("m_alpha", c_void_p),
+                ("v_alpha", c_void_p)]
+
+
 class BatchMaterial(ctypes.Structure):
     _fields_ = [("latents", Latents), ("mlp", Mlp), ("out_w", c_int32), ("out_h", c_int32), ("out", c_void_p)]
 
@@ -84,6 +91,9 @@ PROTOTYPES = {
     "nbtc_forward_continuous": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
     "nbtc_backward_continuous": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
     "nbtc_train_step_noalloc": (c_int, [POINTER(TrainArgs), c_void_p, c_void_p]),
+    "nbtc_qat_decode": (c_int, [c_void_p, POINTER(QatLevel), c_void_p, c_void_p]),
+    "nbtc_qat_encode": (c_int, [c_void_p, POINTER(QatLevel), c_void_p, c_void_p]),
+    "nbtc_train_step_qat": (c_int, [c_void_p, POINTER(TrainArgs), POINTER(QatLevel), c_void_p, c_void_p]),
     "nbtc_batch_create": (c_int, [c_void_p, POINTER(BatchMaterial), c_int32, POINTER(Frame), c_int32,
                                   POINTER(c_void_p), c_void_p]),
     "nbtc_decode_batched": (c_int, [c_void_p, c_void_p, c_void_p]),

@@ -279,6 +279,25 @@ nbtc_status nbtc_train_step(nbtc_context* ctx, const nbtc_train_args* args, floa
                          args->workspace_bytes);
 }
 
+nbtc_status nbtc_qat_decode(nbtc_context* ctx, const nbtc_qat_level* level, float* out, void* stream) {
+  nbtc_status st = enter(ctx);
+  if (st) return st;
+  return qat_decode(ctx, level, out, (cudaStream_t)stream);
+}
+
+nbtc_status nbtc_qat_encode(nbtc_context* ctx, const nbtc_qat_level* level, uint64_t* blocks, void* stream) {
+  nbtc_status st = enter(ctx);
+  if (st) return st;
+  return qat_encode(ctx, level, blocks, (cudaStream_t)stream);
+}
+
+nbtc_status nbtc_train_step_qat(nbtc_context* ctx, const nbtc_train_args* args, const nbtc_qat_level* levels,
+                                float* loss_dev, void* stream) {
+  nbtc_status st = enter(ctx);
+  if (st) return st;
+  return train_step_qat(ctx, args, levels, loss_dev, (cudaStream_t)stream);
+}
+
 nbtc_status nbtc_forward_continuous(nbtc_context* ctx, const nbtc_train_args* args, float* y_dev, void* stream) {
   nbtc_status st = enter(ctx);
   if (st) return st;

@@ -46,9 +46,18 @@ nbtc_status launch_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int precisio
 nbtc_status launch_decode_tc(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, int precision,
                              const void* packed, cudaStream_t s);
 size_t train_workspace(nbtc_context* ctx, const nbtc_train_args* A);
-// mode: 0 forward (y), 1 backward from dy, 2 full step (loss, grads, Adam)
+// mode: 0 forward (y), 1 backward from dy, 2 full step (loss, grads, Adam), 3 full step
+// without the latent Adam (latent gradients only)
 nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* loss, cudaStream_t s, int mode,
                             const float* dy, float* y, void* workspace, size_t workspace_bytes);
+// QAT BC1 latents (qat.cu).
+nbtc_status qat_decode(nbtc_context* ctx, const nbtc_qat_level* q, float* out, cudaStream_t s);
+nbtc_status qat_encode(nbtc_context* ctx, const nbtc_qat_level* q, uint64_t* blocks, cudaStream_t s);
+nbtc_status train_step_qat(nbtc_context* ctx, const nbtc_train_args* A, const nbtc_qat_level* levels, float* loss,
+                           cudaStream_t s);
+// One Adam update (the step's betas, eps and step number; learning rate lr) of n parameters.
+nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, float* p, const float* g, float* m,
+                        float* v, int64_t n, cudaStream_t s);
 nbtc_status launch_calibrate_fp32(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp,
                                   int step, float* absmax, cudaStream_t s);
 

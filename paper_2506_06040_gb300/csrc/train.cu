@@ -453,7 +453,23 @@ __global__ void k_adam_latent(float* __restrict__ p, const float* __restrict__ g
 
 // ------------------------------------------------------------------ host
 
-static nbtc_status check_train(const nbtc_train_args* A, bool need_target, bool need_adam) {
+nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, float* p, const float* g, float* m,
+                        float* v, int64_t n, cudaStream_t s) {
+  AdamHyper h;
+  h.b1 = A->beta1;
+  h.b2 = A->beta2;
+  h.eps = A->eps;
+  h.bc1 = (float)(1.0 - pow((double)A->beta1, (double)A->step));
+  h.bc2 = (float)(1.0 - pow((double)A->beta2, (double)A->step));
+  h.lr = lr;
+  if (n <= 0) return NBTC_OK;
+  int grid = (int)((n + 255) / 256);
+  if (grid > ctx->sm_count * 16) grid = ctx->sm_count * 16;
+  k_adam_latent<<<grid, 256, 0, s>>>(p, g, m, v, n, h);
+  return cuda_check(cudaGetLastError(), "launch k_adam_latent");
+}
+
+static nbtc_status check_train(const nbtc_train_args* A, bool need_target, bool need_adam, bool need_latent_adam) {
   if (!A) return fail(NBTC_ERR_INVALID_ARG, "train args NULL");
   if (A->num_levels != 4) return fail(NBTC_ERR_UNSUPPORTED, "training takes 4 latent levels");
   const nbtc_mlp& m = A->mlp;
@@ -465,7 +481,8 @@ static nbtc_status check_train(const nbtc_train_args* A, bool need_target, bool 
     if (!A->latents[k] || !A->latent_grads[k]) return fail(NBTC_ERR_INVALID_ARG, "latent or gradient NULL");
     if (A->widths[k] < 1 || A->heights[k] < 1 || A->widths[k] > (1 << 15) || A->heights[k] > (1 << 15))
       return fail(NBTC_ERR_INVALID_ARG, "latent size out of range");
-    if (need_adam && (!A->latent_m[k] || !A->latent_v[k])) return fail(NBTC_ERR_INVALID_ARG, "latent moments NULL");
+    if (need_latent_adam && (!A->latent_m[k] || !A->latent_v[k]))
+      return fail(NBTC_ERR_INVALID_ARG, "latent moments NULL");
   }
   if (!A->grad_w || !A->grad_b) return fail(NBTC_ERR_INVALID_ARG, "grad_w / grad_b NULL");
   if (need_adam && (!A->m_w || !A->v_w || !A->m_b || !A->v_b)) return fail(NBTC_ERR_INVALID_ARG, "MLP moments NULL");
@@ -536,7 +553,10 @@ static nbtc_status zero_latent_grads(const nbtc_train_args* A, cudaStream_t s) {
 
 nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* loss, cudaStream_t s, int mode,
                             const float* dy, float* y, void* workspace, size_t workspace_bytes) {
-  nbtc_status st = check_train(A, mode == kModeTrain, mode == kModeTrain);
+  // mode 3: the full step without the latent Adam (the QAT step updates its raw parameters itself)
+  const bool latent_adam = mode == kModeTrain;
+  if (mode == 3) mode = kModeTrain;
+  nbtc_status st = check_train(A, mode == kModeTrain, mode == kModeTrain, latent_adam);
   if (st) return st;
   const int grid = train_grid(ctx, A->batch);
   TrainDev d = make_dev(A, workspace);
@@ -572,7 +592,7 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
                                                  A->grad_b, A->m_w, A->v_w, A->m_b, A->v_b, loss,
                                                  mode == kModeTrain ? 1 : 0, h);
   if ((st = cuda_check(cudaGetLastError(), "launch k_reduce_adam"))) return st;
-  if (mode == kModeTrain) {
+  if (latent_adam) {
     h.lr = A->lr_latent;
     for (int k = 0; k < 4; ++k) {
       const int64_t n = 3 * (int64_t)A->widths[k] * A->heights[k];

@@ -132,3 +132,58 @@ class NbtcDecodeFn(torch.autograd.Function):
         ctx, model, uv, lats, w, b = fctx.saved
         model.backward(ctx, uv, dy.contiguous().float(), latents=lats, weights=w, biases=b)
         return (None, None, None, *[g.clone() for g in model.latent_grads], model.grad_w.clone(), model.grad_b.clone())
+
+
+class QatModel(ContinuousModel):
+    """Quantisation-aware BC1 latents (Sec. 3.2, Eqs. 1-3) + MLP [12, 64, 64, C]:
+    per level raw endpoints e0, e1 [h/4, w/4, 3] and blend factors alpha [h, w]
+    with their gradients and Adam moments.  The decoded textures (and their
+    gradients) live in the base class's latent buffers, rewritten every step."""
+
+    def __init__(self, e0, e1, alpha, shifts, weights, biases, device="cuda"):
+        dev = torch.device(device)
+        f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+        decoded = [np.zeros((a.shape[0], a.shape[1], 3), np.float32) for a in alpha]
+        super().__init__(decoded, shifts, weights, biases, device)
+        self.e0, self.e1, self.alpha = [f32(a) for a in e0], [f32(a) for a in e1], [f32(a) for a in alpha]
+        z = torch.zeros_like
+        self.g_e0, self.g_e1, self.g_alpha = [z(a) for a in self.e0], [z(a) for a in self.e1], [z(a) for a in self.alpha]
+        self.m_e0, self.v_e0 = [z(a) for a in self.e0], [z(a) for a in self.e0]
+        self.m_e1, self.v_e1 = [z(a) for a in self.e1], [z(a) for a in self.e1]
+        self.m_alpha, self.v_alpha = [z(a) for a in self.alpha], [z(a) for a in self.alpha]
+
+    def level(self, k) -> _abi.QatLevel:
+        q = _abi.QatLevel()
+        q.height, q.width = int(self.alpha[k].shape[0]), int(self.alpha[k].shape[1])
+        for name in ("e0", "e1", "alpha", "g_e0", "g_e1", "g_alpha", "m_e0", "v_e0", "m_e1", "v_e1", "m_alpha",
+                     "v_alpha"):
+            setattr(q, name, getattr(self, name)[k].data_ptr())
+        return q
+
+    def decode_level(self, ctx, k, stream=None) -> torch.Tensor:
+        """Decoded texture [h, w, 3] of level k from the current raw parameters."""
+        q = self.level(k)
+        out = torch.empty((q.height, q.width, 3), dtype=torch.float32, device=self.device)
+        s = c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+        check(ctx.lib.nbtc_qat_decode(ctx.handle, byref(q), _p(out), s))
+        return out
+
+    def encode_level(self, ctx, k, stream=None) -> torch.Tensor:
+        """BC1 blocks (int64 view of the uint64 words) of level k."""
+        q = self.level(k)
+        out = torch.empty((q.height // 4) * (q.width // 4), dtype=torch.int64, device=self.device)
+        s = c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+        check(ctx.lib.nbtc_qat_encode(ctx.handle, byref(q), _p(out), s))
+        return out
+
+    def train_step(self, ctx, uv, target, loss=_abi.LOSS_MSE, stream=None, **kw) -> torch.Tensor:
+        """One QAT step (decode, forward, loss, backward, straight-through
+        backward, Adam on MLP and raw parameters); returns the batch loss."""
+        a = self.args(uv, target, loss, **kw)
+        self._workspace(ctx, a)
+        levels = (_abi.QatLevel * 4)(*[self.level(k) for k in range(4)])
+        out = torch.empty(1, dtype=torch.float32, device=self.device)
+        s = c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+        check(ctx.lib.nbtc_train_step_qat(ctx.handle, byref(a), levels, _p(out), s))
+        self.step_count += 1
+        return out
