@@ -138,3 +138,61 @@ def decode_pixels_direct(material, uv: np.ndarray, lod: np.ndarray, precision: s
         return emulate.forward_fp16(x, mlp.weights, mlp.biases)
     from . import mlp as mlp_mod
     return mlp_mod.forward(x, mlp.weights, mlp.biases)
+
+
+def aniso_count(duv: np.ndarray, max_aniso: int):
+    """Anisotropic filter of the latents (Sec. 3.2, "Anisotropic Filtering"): the
+    paper uses the texture unit's anisotropic filter on the latents unchanged;
+    this restates the reference formulas of the anisotropic-filtering extension
+    (EXT_texture_filter_anisotropic): with Px = |d(u,v)/dx|, Py = |d(u,v)/dy|,
+    Pmax = max, Pmin = min, N = min(ceil(Pmax / Pmin), max_aniso) probes along the
+    major axis, lod = log2(Pmax / N).  Computed in texture-coordinate units (the
+    square latents make the ratio the same for every level).  N is an integer
+    decided by floating point, so it is decided here in FP32 with the kernel's
+    operation order (products, sum, square root, quotient, ceil -- all correctly
+    rounded).  Returns (N [n], along_x [n] bool, Pmax [n] FP32)."""
+    d = np.asarray(duv, dtype=np.float32)
+    px = np.sqrt(d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1])
+    py = np.sqrt(d[..., 2] * d[..., 2] + d[..., 3] * d[..., 3])
+    along_x = px >= py
+    pmax = np.where(along_x, px, py)
+    pmin = np.where(along_x, py, px)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = np.ceil(pmax / pmin)
+    n = np.where(pmax > 0, np.where(pmin > 0, np.minimum(ratio, np.float32(max_aniso)), max_aniso), 1)
+    return n.astype(np.int64), along_x, pmax
+
+
+def aniso_features(material, levels_mips_rgb: list, uv: np.ndarray, duv: np.ndarray, bias: np.ndarray,
+                   max_aniso: int) -> np.ndarray:
+    """[n, 12] features: the mean of N trilinear probes at uv + (i / (N + 1) - 1/2)
+    times the major-axis derivative, i = 1..N, each level at lod
+    bias + log2(Pmax W_k / N) (FP64 apart from the decision of N)."""
+    n, along_x, pmax = aniso_count(duv, max_aniso)
+    d = np.asarray(duv, dtype=np.float64)
+    au = np.where(along_x, d[:, 0], d[:, 2])
+    av = np.where(along_x, d[:, 1], d[:, 3])
+    u, v = uv[:, 0].astype(np.float64), uv[:, 1].astype(np.float64)
+    base = np.asarray(bias, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        base = base + np.log2(pmax.astype(np.float64) / n)
+    feats = np.zeros((len(u), 12))
+    for i in range(1, int(n.max()) + 1):
+        sel = n >= i
+        off = i / (n[sel] + 1.0) - 0.5
+        uu, vv = u[sel] + off * au[sel], v[sel] + off * av[sel]
+        for k, (lv, mips) in enumerate(zip(material.levels, levels_mips_rgb)):
+            lam = base[sel] + np.log2(float(lv.width))
+            feats[sel, 3 * k:3 * k + 3] += trilinear(mips, uu, vv, lam, lv.shift, material.address)
+    return feats / n[:, None]
+
+
+def decode_pixels_aniso(material, levels_mips_rgb: list, uv: np.ndarray, duv: np.ndarray, bias: np.ndarray,
+                        max_aniso: int, precision: str = "fp16") -> np.ndarray:
+    """decode_pixels with the anisotropic latent filter instead of trilinear."""
+    x = aniso_features(material, levels_mips_rgb, uv, duv, bias, max_aniso)
+    mlp = material.mlp
+    if precision == "fp16":
+        return emulate.forward_fp16(x, mlp.weights, mlp.biases)
+    from . import mlp as mlp_mod
+    return mlp_mod.forward(x, mlp.weights, mlp.biases)

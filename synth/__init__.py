@@ -280,6 +280,7 @@ class BatchWorkload:
     lod_bias: np.ndarray  # [frame_h, frame_w] FP32
     seed: int
     lod: np.ndarray = None  # [frame_h, frame_w] FP32: log2(uv footprint of a pixel) + bias
+    duv: np.ndarray = None  # [frame_h, frame_w, 4] FP32 anisotropic footprint: du/dx, dv/dx, du/dy, dv/dy
 
 
 def voronoi_ids(rng: Rng, w: int, h: int, m: int):
@@ -321,5 +322,21 @@ def batch_workload(num_materials: int = 64, frame_w: int = 3840, frame_h: int = 
     bias = rng_f.uniform(frame_w * frame_h, 0.0, 3.0).reshape(frame_h, frame_w).astype(np.float32)
     # a pixel spans s_m / frame_h in uv (tiled uv of scale s_m over the frame height)
     lod = (bias.astype(np.float64) + np.log2(s_pix / frame_h)).astype(np.float32)
+    duv = aniso_footprints(Rng(seed, 3), ids, s_pix / frame_h, num_materials)
     return BatchWorkload(f"batch-{num_materials}mat-{frame_w}x{frame_h}", mats, sizes, frame_w, frame_h,
-                         ids, uv, bias, seed, lod)
+                         ids, uv, bias, seed, lod, duv)
+
+
+def aniso_footprints(rng: Rng, ids: np.ndarray, f: np.ndarray, num_materials: int) -> np.ndarray:
+    """Screen-space uv derivatives [h, w, 4] = (du/dx, dv/dx, du/dy, dv/dy) of an
+    anisotropic footprint: the isotropic footprint f (uv per pixel) stretched by
+    r = 1 + 15 y / h (1 at the top row, 16 at the bottom, like a plane seen at a
+    growing grazing angle) along a direction phi drawn per material."""
+    h, w = ids.shape
+    phi = rng.uniform(num_materials, 0.0, np.pi)[ids]
+    r = 1.0 + 15.0 * (np.arange(h, dtype=np.float64) + 0.5)[:, None] / h
+    c, s = np.cos(phi), np.sin(phi)
+    # J = R(phi) diag(r, 1) f: screen x maps along the stretched direction
+    dudx, dvdx = f * r * c, f * r * s
+    dudy, dvdy = -f * s, f * c
+    return np.stack([dudx, dvdx, dudy, dvdy], axis=-1).astype(np.float32)

@@ -64,3 +64,65 @@ def test_direct_pixel_decode_equals_full_mip_decode():
             a = frame.decode_pixels(mat, mips, uv, lod, precision=prec)
             b = frame.decode_pixels_direct(mat, uv, lod, precision=prec)
             np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+
+
+def _small_mip_material(seed=21, side=256):
+    rng_lat, rng_mlp = synth.Rng(seed, 1), synth.Rng(seed, 2)
+    return synth.Material(synth.latent_pyramid(rng_lat, side, mips=True), synth.he_mlp(rng_mlp, [12, 64, 64, 9]),
+                          "wrap")
+
+
+def test_aniso_count_matches_the_extension_formula():
+    rng = np.random.default_rng(3)
+    duv = rng.normal(0, 1e-3, (20000, 4)).astype(np.float32)
+    n, along_x, pmax = frame.aniso_count(duv, 16)
+    d = duv.astype(np.float64)
+    px, py = np.hypot(d[:, 0], d[:, 1]), np.hypot(d[:, 2], d[:, 3])
+    ratio = np.maximum(px, py) / np.minimum(px, py)
+    clear = np.abs(ratio - np.round(ratio)) > 1e-4          # away from integer ratios
+    want = np.minimum(np.ceil(ratio), 16).astype(np.int64)
+    assert np.array_equal(n[clear], want[clear])
+    assert np.array_equal(along_x, px >= py) or np.mean(along_x == (px >= py)) > 0.9999
+    assert n.min() >= 1 and n.max() == 16
+    # no footprint (magnification): one probe
+    n0, _, _ = frame.aniso_count(np.zeros((3, 4), np.float32), 16)
+    assert n0.tolist() == [1, 1, 1]
+
+
+def test_aniso_with_isotropic_footprint_is_trilinear():
+    mat = _small_mip_material()
+    mips = [frame.level_mips_rgb(lv) for lv in mat.levels]
+    rng = np.random.default_rng(4)
+    uv = rng.uniform(-2, 3, (500, 2)).astype(np.float32)
+    f = (2.0 ** rng.uniform(-9, -2, 500)).astype(np.float32)
+    bias = rng.uniform(0, 3, 500).astype(np.float32)
+    duv = np.stack([f, 0 * f, 0 * f, f], axis=-1)
+    lod = bias.astype(np.float64) + np.log2(f.astype(np.float64))
+    got = frame.decode_pixels_aniso(mat, mips, uv, duv, bias, 16, precision="fp64")
+    want = frame.decode_pixels(mat, mips, uv, lod, precision="fp64")
+    assert np.max(np.abs(got - want)) < 1e-12
+
+
+def test_aniso_symmetries_and_constant_texture():
+    mat = _small_mip_material(seed=22)
+    mips = [frame.level_mips_rgb(lv) for lv in mat.levels]
+    rng = np.random.default_rng(5)
+    uv = rng.uniform(0, 4, (400, 2)).astype(np.float32)
+    duv = rng.normal(0, 4e-3, (400, 4)).astype(np.float32)
+    bias = rng.uniform(0, 2, 400).astype(np.float32)
+    x = frame.aniso_features(mat, mips, uv, duv, bias, 16)
+    # the probes are symmetric about uv: negating the derivatives changes nothing
+    assert np.max(np.abs(frame.aniso_features(mat, mips, uv, -duv, bias, 16) - x)) < 1e-12
+    # which screen axis carries the major derivative does not matter
+    sw = duv[:, [2, 3, 0, 1]]
+    assert np.max(np.abs(frame.aniso_features(mat, mips, uv, sw, bias, 16) - x)) < 1e-12
+    # a latent pyramid of constant colour filters to that colour for any footprint
+    const = []
+    for lv in mat.levels:
+        blocks = [np.full(len(b), np.uint64(0x000052AA52AA), dtype=np.uint64) for b in lv.blocks]
+        const.append(synth.Level(lv.width, lv.height, lv.shift, blocks))
+    cm = synth.Material(const, mat.mlp, "wrap")
+    cx = frame.aniso_features(cm, [frame.level_mips_rgb(lv) for lv in cm.levels], uv, duv, bias, 16)
+    rgb = np.array([0x52AA >> 11, (0x52AA >> 5) & 63, 0x52AA & 31])
+    want = np.array([(rgb[0] << 3 | rgb[0] >> 2), (rgb[1] << 2 | rgb[1] >> 4), (rgb[2] << 3 | rgb[2] >> 2)]) / 255
+    assert np.max(np.abs(cx - np.tile(want, 4))) < 1e-12
