@@ -292,7 +292,16 @@ nbtc_status nbtc_train_step_qat(nbtc_context* ctx, const nbtc_train_args* args, 
  * B packs the valid pixels of mixed tiles into 128-slot tiles of one material.
  * Each pixel is then decoded with per-level lod_k = lod + log2(W_k) (clamped to
  * the level's mips, trilinear) and its material's MLP; the C FP16 channels go
- * to out[pixel].  Pixels with id -1 are left untouched. */
+ * to out[pixel].  Pixels with id -1 are left untouched.
+ *
+ * Anisotropic latent filter (Sec. 3.2 "Anisotropic Filtering": the latents are
+ * fetched with the anisotropic filter a renderer uses; the reference formulas
+ * of the anisotropic-filtering extension): with Px = |(du/dx, dv/dx)|,
+ * Py = |(du/dy, dv/dy)|, Pmax / Pmin their max / min, N = min(ceil(Pmax / Pmin),
+ * max_aniso) (1 when Pmax = 0; decided in FP32), every level is sampled by N
+ * trilinear probes at uv + (i / (N + 1) - 1/2) d, i = 1..N, d the derivative
+ * of the major axis, at lod_k = bias + log2(Pmax W_k / N), and the probes are
+ * averaged. */
 typedef struct {
   nbtc_latents latents;   /* 4 levels (with mips for the frame) */
   nbtc_mlp mlp;           /* FP32 [12, 64, .., 64, C]; the same depth and C for every material */
@@ -304,8 +313,11 @@ typedef struct {
   int32_t width, height;  /* pixels */
   const int32_t* mat_id;  /* [height][width] material index or -1 */
   const float* uv;        /* [height][width][2] */
-  const float* lod;       /* [height][width] */
+  const float* lod;       /* [height][width]: lod, or the mip bias when duv is set */
   void* out;              /* FP16 [height][width][C] */
+  const float* duv;       /* NULL, or [height][width][4] (du/dx, dv/dx, du/dy, dv/dy), 16-byte aligned:
+                             anisotropic latent filter (see below) */
+  int32_t max_aniso;      /* probes cap of the anisotropic filter, 1..16 */
 } nbtc_frame;
 
 typedef struct nbtc_batch nbtc_batch;

@@ -58,7 +58,7 @@ class BatchMaterial(ctypes.Structure):
 
 class Frame(ctypes.Structure):
     _fields_ = [("width", c_int32), ("height", c_int32), ("mat_id", c_void_p), ("uv", c_void_p),
-                ("lod", c_void_p), ("out", c_void_p)]
+                ("lod", c_void_p), ("out", c_void_p), ("duv", c_void_p), ("max_aniso", c_int32)]
 
 
 class BatchInfo(ctypes.Structure):

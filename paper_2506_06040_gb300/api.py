@@ -164,7 +164,8 @@ class Batch:
 
     materials: list of Material; outs: list of (tensor FP16 [h*w, C], w, h) or
     None per material; frame: dict(mat_id int32 [h, w], uv FP32 [h, w, 2],
-    lod FP32 [h, w], out FP16 [h, w, C]) or None."""
+    lod FP32 [h, w], out FP16 [h, w, C], and optionally duv FP32 [h, w, 4] with
+    max_aniso for the anisotropic latent filter -- lod is then the mip bias) or None."""
 
     def __init__(self, ctx: Context, materials, outs=None, frame=None, autotune=True, stream=None):
         self.ctx = ctx
@@ -184,6 +185,8 @@ class Batch:
             fr.height, fr.width = int(frame["mat_id"].shape[0]), int(frame["mat_id"].shape[1])
             fr.mat_id, fr.uv, fr.lod, fr.out = (frame["mat_id"].data_ptr(), frame["uv"].data_ptr(),
                                                 frame["lod"].data_ptr(), frame["out"].data_ptr())
+            if frame.get("duv") is not None:
+                fr.duv, fr.max_aniso = frame["duv"].data_ptr(), int(frame.get("max_aniso", 16))
         h = c_void_p()
         flags = _abi.BATCH_AUTOTUNE if autotune else 0
         check(ctx.lib.nbtc_batch_create(ctx.handle, arr, len(self.materials), byref(fr) if fr is not None else None,

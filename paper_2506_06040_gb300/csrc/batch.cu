@@ -268,6 +268,8 @@ static nbtc_status enqueue_render(nbtc_context* ctx, nbtc_batch* B, cudaStream_t
   p.fmat = B->frame.mat_id;
   p.fuv = B->frame.uv;
   p.flod = B->frame.lod;
+  p.fduv = B->frame.duv;
+  p.max_aniso = B->frame.duv ? B->frame.max_aniso : 1;
   p.fout = static_cast<uint16_t*>(B->frame.out);
   p.frame_w = F.w;
   p.tile_w = F.tw;
@@ -398,6 +400,8 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     if (frame->width <= 0 || frame->height <= 0 || !frame->mat_id || !frame->uv || !frame->lod || !frame->out)
       return fail(NBTC_ERR_INVALID_ARG, "frame buffers NULL or size <= 0");
     if (!aligned(frame->uv, 8)) return fail(NBTC_ERR_INVALID_ARG, "frame uv not 8-byte aligned");
+    if (frame->duv && (!aligned(frame->duv, 16) || frame->max_aniso < 1 || frame->max_aniso > 16))
+      return fail(NBTC_ERR_INVALID_ARG, "frame duv not 16-byte aligned or max_aniso outside 1..16");
     if ((int64_t)frame->width * frame->height >= (int64_t)1 << 31) return fail(NBTC_ERR_UNSUPPORTED, "frame too large");
   }
   nbtc_batch* B = new nbtc_batch();

@@ -340,6 +340,48 @@ __device__ __forceinline__ void trilinear_features(const MatDev& M, float u, flo
   }
 }
 
+// Anisotropic latent filter of one frame pixel (the reference formulas of the
+// anisotropic-filtering extension, in texture-coordinate units -- the square
+// latents make Pmax / Pmin the same for every level): N = min(ceil(Pmax /
+// Pmin), max_aniso) trilinear probes at uv + (i / (N + 1) - 1/2) d along the
+// major-axis derivative d, each level at lod bias + log2(Pmax W_k / N),
+// averaged.  N is decided with correctly rounded FP32 operations in a fixed
+// order (no contraction), so any IEEE implementation decides it alike.
+__device__ __forceinline__ void aniso_features(const MatDev& M, float u, float v, float4 d, float bias,
+                                               int max_aniso, float (&feat)[12]) {
+  const float px = __fsqrt_rn(__fadd_rn(__fmul_rn(d.x, d.x), __fmul_rn(d.y, d.y)));
+  const float py = __fsqrt_rn(__fadd_rn(__fmul_rn(d.z, d.z), __fmul_rn(d.w, d.w)));
+  const bool along_x = px >= py;
+  const float pmax = along_x ? px : py, pmin = along_x ? py : px;
+  int n = 1;
+  if (pmax > 0.f) n = pmin > 0.f ? (int)fminf(ceilf(__fdiv_rn(pmax, pmin)), (float)max_aniso) : max_aniso;
+  const float au = along_x ? d.x : d.z, av = along_x ? d.y : d.w;
+  const float base = bias + log2f(pmax / (float)n);  // -inf for a zero footprint: clamps to mip 0
+  const bool wrap = M.d.wrap;
+  float acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = 0.f;
+  for (int i = 1; i <= n; ++i) {
+    const float off = (float)i / (float)(n + 1) - 0.5f;
+    const float uu = fmaf(off, au, u), vv = fmaf(off, av, v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float lam = fminf(fmaxf(base + M.log2w[k], 0.f), (float)(M.mips[k] - 1));
+      const int m0 = (int)floorf(lam);
+      const int m1 = min(m0 + 1, M.mips[k] - 1);
+      const float t = lam - (float)m0;
+      const float3 c0 = sample_bilinear(mip_view(M, k, m0), uu, vv, wrap);
+      const float3 c1 = sample_bilinear(mip_view(M, k, m1), uu, vv, wrap);
+      acc[3 * k + 0] += fmaf(t, c1.x - c0.x, c0.x);
+      acc[3 * k + 1] += fmaf(t, c1.y - c0.y, c0.y);
+      acc[3 * k + 2] += fmaf(t, c1.z - c0.z, c0.z);
+    }
+  }
+  const float inv = 1.0f / (float)n;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) feat[c] = acc[c] * inv;
+}
+
 // Features of one texel sampled on its own (any uv).
 __device__ __forceinline__ void direct_features(const DecodeArgs& a, int64_t t, float (&feat)[12]) {
   const float2 uv = texel_uv(a, t);

@@ -83,7 +83,9 @@ struct TcArgs {
   const int* plist;        // frame: packed pixel indices (128 per tile, -1 = none)
   const int* fmat;         // frame: per-pixel material id
   const float* fuv;        // frame: per-pixel uv
-  const float* flod;       // frame: per-pixel lod (log2 of the uv footprint + bias)
+  const float* flod;       // frame: per-pixel lod (log2 of the uv footprint + bias), or the bias with fduv
+  const float* fduv;       // frame: per-pixel uv derivatives (anisotropic filter) or NULL
+  int max_aniso;           // frame: probe cap of the anisotropic filter
   uint16_t* fout;          // frame: per-pixel output (nout FP16)
   int frame_w, tile_w, tile_h, tiles_x;
 };

@@ -303,7 +303,11 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
           const int64_t px = frame_pixel(p, work.c, T, gt);
           const int64_t pq = px < 0 ? 0 : px;
           const float2 uv = __ldg(reinterpret_cast<const float2*>(p.fuv) + pq);
-          trilinear_features(work.m, uv.x, uv.y, __ldg(p.flod + pq), f);
+          if (p.fduv)
+            aniso_features(work.m, uv.x, uv.y, __ldg(reinterpret_cast<const float4*>(p.fduv) + pq), __ldg(p.flod + pq),
+                           p.max_aniso, f);
+          else
+            trilinear_features(work.m, uv.x, uv.y, __ldg(p.flod + pq), f);
         }
         if constexpr (!FP8) {
           sts128(a0 + off_interleave(gt, 0), cvt_f16x2(f[0], f[1]), cvt_f16x2(f[2], f[3]), cvt_f16x2(f[4], f[5]),

@@ -118,6 +118,34 @@ def test_frame_without_autotune_all_pixels(nb, ctx, shape):
     plan.close()
 
 
+@pytest.mark.parametrize("max_aniso", [16, 4])
+def test_frame_anisotropic_filter_all_pixels(nb, ctx, max_aniso):
+    """The frame with the anisotropic latent filter (footprints stretched 1x..16x
+    down the frame along per-material directions): every pixel against the
+    oracle's filter + FP16 emulator."""
+    bw = synth.batch_workload(num_materials=5, frame_w=256, frame_h=128, smin=256, smax=512, seed=78)
+    mats = [nb.Material.from_synth(m) for m in bw.materials]
+    fr = _frame_tensors(bw)
+    fr["lod"] = torch.from_numpy(np.ascontiguousarray(bw.lod_bias)).cuda()
+    fr["duv"] = torch.from_numpy(np.ascontiguousarray(bw.duv)).cuda()
+    fr["max_aniso"] = max_aniso
+    plan = nb.Batch(ctx, mats, None, fr, autotune=False)
+    plan.render()
+    ctx.sync()
+    got = fr["out"].view(-1, 9).float().cpu().numpy().astype(np.float64)
+    ids = bw.mat_id.reshape(-1)
+    uv, duv, bias = bw.uv.reshape(-1, 2), bw.duv.reshape(-1, 4), bw.lod_bias.reshape(-1)
+    n, _, _ = oracle.frame.aniso_count(duv, max_aniso)
+    assert n.max() == max_aniso and n.min() <= 2
+    for m in np.unique(ids[ids >= 0]):
+        sel = ids == m
+        mat = bw.materials[m]
+        mips = [oracle.frame.level_mips_rgb(lv) for lv in mat.levels]
+        emu = oracle.frame.decode_pixels_aniso(mat, mips, uv[sel], duv[sel], bias[sel], max_aniso, "fp16")
+        _check(got[sel], emu, mat, FEATURE_BOUND(int(sel.sum())), 2.0 ** -10, FRAC)
+    plan.close()
+
+
 def test_full_size_batch(nb, ctx):
     """64 materials of 256^2..4096^2 and a 3840x2160 frame, as the benchmark runs
     them: sampled texels of every material and 20,000 frame pixels."""
