@@ -16,4 +16,4 @@ fixed by the format definition, closed forms, library routines (numpy float16,
 torch float8_e4m3fn, scipy map_coordinates, torch float64 linear layers),
 invariants and finite differences.  No function is "parity unpinned".
 """
-from . import bc1, sample, mlp, quant, emulate, train, frame, decode, qat  # noqa: F401
+from . import bc1, sample, mlp, quant, emulate, train, frame, decode, qat, shade  # noqa: F401
