@@ -241,6 +241,33 @@ def run_forms(args, nb, ctx, stream, flush, peaks, sm_count) -> dict:
     return res
 
 
+def run_dsweep(args, nb, ctx, stream, flush) -> dict:
+    """Table 2's sweep on GB300: the paper's one-hidden-layer MLP 12-D-9 for
+    D = 16, 32, 64 on both latent layouts (variant A: 1/4, 1/4, 1/8, 1/8 of the
+    output side; variant B: 1/4, 1/8, 1/16, 1/32), FP32 SIMT form vs FP16
+    tensor-core form, 4096^2 texel grid.  Gtexel/s per case."""
+    import torch
+    side = 4096
+    n = side * side
+    out32 = torch.empty((n, 9), dtype=torch.float32, device="cuda")
+    out16 = torch.empty((n, 9), dtype=torch.float16, device="cuda")
+    res = {"grid": f"{side}x{side}", "cases": []}
+    for layout, ratios in (("A", (4, 4, 8, 8)), ("B", (4, 8, 16, 32))):
+        for D in (16, 32, 64):
+            wl = synth.small_decode_workload(side, [12, D, 9], seed=1100 + D, level_sides=[side // r for r in ratios])
+            mat = nb.Material.from_synth(wl.material)
+            packed = nb.pack_mlp(ctx, mat, nb.FP16, stream=stream)
+            t32 = _time_steps(lambda: nb.decode(ctx, mat, nb.FP32, grid=(side, side), out=out32, stream=stream),
+                              3, 2, flush, stream)
+            t16 = _time_steps(lambda: nb.decode(ctx, mat, nb.FP16, packed, grid=(side, side), out=out16,
+                                                stream=stream), 5, 3, flush, stream)
+            ms32, ms16 = statistics.mean(t32), statistics.mean(t16)
+            res["cases"].append({"layout": layout, "D": D, "fp32_gtexel_s": n / ms32 / 1e6,
+                                 "fp16_tc_gtexel_s": n / ms16 / 1e6, "fp32_ms": ms32, "fp16_tc_ms": ms16})
+    ctx.sync(stream)
+    return res
+
+
 def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
     """One optimisation step on continuous latents (latents 1024^2..128^2, target
     2048^2 x 9, batch 2^20 uniform uv, MLP 12-64-64-9, MSE, Adam): forward, loss,
@@ -415,6 +442,8 @@ def run_ours(args) -> dict | None:
     }
     if "forms" in args.parts:
         res["forms"] = run_forms(args, nb, ctx, stream, flush, peaks, sm_count)
+    if "dsweep" in args.parts:
+        res["dsweep"] = run_dsweep(args, nb, ctx, stream, flush)
     if "train" in args.parts:
         res["train"] = run_train(args, nb, ctx, stream, flush, sm_count, peaks)
     if "batch" in args.parts:
@@ -490,8 +519,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--parts", default="main,forms,train,batch",
-                    help="comma list: main (always), forms, train, batch")
+    ap.add_argument("--parts", default="main,forms,dsweep,train,batch",
+                    help="comma list: main (always), forms, dsweep, train, batch")
     ap.add_argument("--form-side", type=int, default=4096, help="output side of the precision-form workload")
     ap.add_argument("--side", type=int, default=4096, help="output side (4096 = the benchmark workload; "
                     "smaller sides are for profiling captures)")

@@ -301,7 +301,17 @@ nbtc_status nbtc_train_step_qat(nbtc_context* ctx, const nbtc_train_args* args, 
  * max_aniso) (1 when Pmax = 0; decided in FP32), every level is sampled by N
  * trilinear probes at uv + (i / (N + 1) - 1/2) d, i = 1..N, d the derivative
  * of the major axis, at lod_k = bias + log2(Pmax W_k / N), and the probes are
- * averaged. */
+ * averaged.
+ *
+ * Lighting pass (Sec. 4 "Rendering architecture", fused into the frame
+ * decode's epilogue when `shaded` is set; needs C >= 8): the decoded channels
+ * are read as albedo RGB, tangent-space normal XY encoded (n + 1) / 2,
+ * roughness, metalness and ambient occlusion, and shaded with a Lambert
+ * diffuse lobe and a GGX specular lobe (height-correlated Smith visibility,
+ * Schlick Fresnel) under the directional light, plus a two-colour hemisphere
+ * (ground -> sky along z; no environment maps here) sampled at the normal for
+ * the diffuse part and at the reflection vector for the specular part, scaled
+ * by the occlusion.  Directions need not be normalised. */
 typedef struct {
   nbtc_latents latents;   /* 4 levels (with mips for the frame) */
   nbtc_mlp mlp;           /* FP32 [12, 64, .., 64, C]; the same depth and C for every material */
@@ -318,6 +328,11 @@ typedef struct {
   const float* duv;       /* NULL, or [height][width][4] (du/dx, dv/dx, du/dy, dv/dy), 16-byte aligned:
                              anisotropic latent filter (see below) */
   int32_t max_aniso;      /* probes cap of the anisotropic filter, 1..16 */
+  float* shaded;          /* NULL, or FP32 [height][width][4]: lighting pass output (linear RGB, 1) */
+  float light_dir[3];     /* lighting pass constants, tangent space: direction toward the light, */
+  float light_rgb[3];     /* its radiance, */
+  float view_dir[3];      /* direction toward the viewer, */
+  float sky[3], ground[3];  /* and the hemisphere standing in for prefiltered environment lighting */
 } nbtc_frame;
 
 typedef struct nbtc_batch nbtc_batch;

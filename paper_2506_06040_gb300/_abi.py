@@ -58,7 +58,9 @@ class BatchMaterial(ctypes.Structure):
 
 class Frame(ctypes.Structure):
     _fields_ = [("width", c_int32), ("height", c_int32), ("mat_id", c_void_p), ("uv", c_void_p),
-                ("lod", c_void_p), ("out", c_void_p), ("duv", c_void_p), ("max_aniso", c_int32)]
+                ("lod", c_void_p), ("out", c_void_p), ("duv", c_void_p), ("max_aniso", c_int32),
+                ("shaded", c_void_p), ("light_dir", c_float * 3), ("light_rgb", c_float * 3),
+                ("view_dir", c_float * 3), ("sky", c_float * 3), ("ground", c_float * 3)]
 
 
 class BatchInfo(ctypes.Structure):

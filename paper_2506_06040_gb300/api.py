@@ -165,7 +165,9 @@ class Batch:
     materials: list of Material; outs: list of (tensor FP16 [h*w, C], w, h) or
     None per material; frame: dict(mat_id int32 [h, w], uv FP32 [h, w, 2],
     lod FP32 [h, w], out FP16 [h, w, C], and optionally duv FP32 [h, w, 4] with
-    max_aniso for the anisotropic latent filter -- lod is then the mip bias) or None."""
+    max_aniso for the anisotropic latent filter -- lod is then the mip bias -- and
+    shaded FP32 [h, w, 4] with light=dict(light_dir, light_rgb, view_dir, sky,
+    ground) for the fused lighting pass) or None."""
 
     def __init__(self, ctx: Context, materials, outs=None, frame=None, autotune=True, stream=None):
         self.ctx = ctx
@@ -187,6 +189,13 @@ class Batch:
                                                 frame["lod"].data_ptr(), frame["out"].data_ptr())
             if frame.get("duv") is not None:
                 fr.duv, fr.max_aniso = frame["duv"].data_ptr(), int(frame.get("max_aniso", 16))
+            if frame.get("shaded") is not None:
+                fr.shaded = frame["shaded"].data_ptr()
+                lt = frame.get("light", {})
+                for name, default in (("light_dir", (0.3, 0.4, 1.0)), ("light_rgb", (3.0, 3.0, 3.0)),
+                                      ("view_dir", (0.0, 0.0, 1.0)), ("sky", (0.6, 0.7, 0.9)),
+                                      ("ground", (0.15, 0.12, 0.1))):
+                    getattr(fr, name)[:] = [float(x) for x in lt.get(name, default)]
         h = c_void_p()
         flags = _abi.BATCH_AUTOTUNE if autotune else 0
         check(ctx.lib.nbtc_batch_create(ctx.handle, arr, len(self.materials), byref(fr) if fr is not None else None,

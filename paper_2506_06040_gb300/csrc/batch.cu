@@ -244,6 +244,36 @@ static nbtc_status enqueue_decode(nbtc_context* ctx, nbtc_batch* B, cudaStream_t
   return launch_tc_args(ctx, p, B->nhid, false, B->W, ctx->sm_count, s);
 }
 
+// Lighting constants of a frame: unit directions and the half vector, in double
+// before rounding to FP32.
+static LightDev make_light(const nbtc_frame& f) {
+  LightDev L;
+  auto unit = [](const float* a, double* o) {
+    const double n = std::sqrt((double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2]);
+    for (int i = 0; i < 3; ++i) o[i] = n > 0 ? a[i] / n : (i == 2 ? 1.0 : 0.0);
+  };
+  double l[3], v[3], h[3];
+  unit(f.light_dir, l);
+  unit(f.view_dir, v);
+  const double hs[3] = {l[0] + v[0], l[1] + v[1], l[2] + v[2]};
+  const double hn = std::sqrt(hs[0] * hs[0] + hs[1] * hs[1] + hs[2] * hs[2]);
+  double ldoth = 0;
+  for (int i = 0; i < 3; ++i) {
+    h[i] = hn > 0 ? hs[i] / hn : (i == 2 ? 1.0 : 0.0);
+    ldoth += l[i] * h[i];
+  }
+  for (int i = 0; i < 3; ++i) {
+    L.l[i] = (float)l[i];
+    L.v[i] = (float)v[i];
+    L.h[i] = (float)h[i];
+    L.rgb[i] = f.light_rgb[i];
+    L.sky[i] = f.sky[i];
+    L.ground[i] = f.ground[i];
+  }
+  L.ldoth = (float)(ldoth > 0 ? ldoth : 0);
+  return L;
+}
+
 static nbtc_status enqueue_render(nbtc_context* ctx, nbtc_batch* B, cudaStream_t s) {
   FrameDev& F = B->F;
   nbtc_status st;
@@ -270,6 +300,8 @@ static nbtc_status enqueue_render(nbtc_context* ctx, nbtc_batch* B, cudaStream_t
   p.flod = B->frame.lod;
   p.fduv = B->frame.duv;
   p.max_aniso = B->frame.duv ? B->frame.max_aniso : 1;
+  p.fshade = B->frame.shaded;
+  p.light = make_light(B->frame);
   p.fout = static_cast<uint16_t*>(B->frame.out);
   p.frame_w = F.w;
   p.tile_w = F.tw;
@@ -402,6 +434,9 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     if (!aligned(frame->uv, 8)) return fail(NBTC_ERR_INVALID_ARG, "frame uv not 8-byte aligned");
     if (frame->duv && (!aligned(frame->duv, 16) || frame->max_aniso < 1 || frame->max_aniso > 16))
       return fail(NBTC_ERR_INVALID_ARG, "frame duv not 16-byte aligned or max_aniso outside 1..16");
+    if (frame->shaded && !aligned(frame->shaded, 16))
+      return fail(NBTC_ERR_INVALID_ARG, "frame shaded output not 16-byte aligned");
+    if (frame->shaded && nout < 8) return fail(NBTC_ERR_UNSUPPORTED, "the lighting pass needs at least 8 channels");
     if ((int64_t)frame->width * frame->height >= (int64_t)1 << 31) return fail(NBTC_ERR_UNSUPPORTED, "frame too large");
   }
   nbtc_batch* B = new nbtc_batch();

@@ -23,9 +23,12 @@ __device__ float scale_for_absmax(float x) {
   return ldexpf(1.f, k);
 }
 
-// One CTA: converts the FP32 MLP into the shared-memory image.
-__global__ void k_pack_mlp(const float* __restrict__ W, const float* __restrict__ B, int nhid, int nin, int nout,
-                           int fp8, const float* __restrict__ act_absmax, unsigned char* __restrict__ out) {
+// One CTA: converts the FP32 MLP into the shared-memory image.  Hidden width
+// `hid` (16, 32 or 64) is zero-padded to the image's 64: the padded neurons have
+// zero weights and bias, so they stay exactly 0 through ReLU and add exact zeros
+// to the next layer's sums.
+__global__ void k_pack_mlp(const float* __restrict__ W, const float* __restrict__ B, int nhid, int nin, int hid,
+                           int nout, int fp8, const float* __restrict__ act_absmax, unsigned char* __restrict__ out) {
   const TcLayout L{nhid, fp8 != 0};
   __shared__ float wmax[8];
   __shared__ float sw[8], sa[8];
@@ -35,7 +38,7 @@ __global__ void k_pack_mlp(const float* __restrict__ W, const float* __restrict_
   // per-layer weight absmax
   int off = 0;
   for (int l = 0; l < nl; ++l) {
-    const int in = l == 0 ? nin : kHid, o = l == nhid ? nout : kHid;
+    const int in = l == 0 ? nin : hid, o = l == nhid ? nout : hid;
     float m = 0.f;
     for (int e = threadIdx.x; e < in * o; e += blockDim.x) m = fmaxf(m, fabsf(W[off + e]));
     atomicMax(reinterpret_cast<int*>(&wmax[l]), __float_as_int(m));
@@ -53,7 +56,7 @@ __global__ void k_pack_mlp(const float* __restrict__ W, const float* __restrict_
   __syncthreads();
   off = 0;
   for (int l = 0; l < nl; ++l) {
-    const int in = l == 0 ? nin : kHid, o = l == nhid ? nout : kHid;
+    const int in = l == 0 ? nin : hid, o = l == nhid ? nout : hid;
     for (int e = threadIdx.x; e < in * o; e += blockDim.x) {
       const int n = e / in, k = e - n * in;
       const float w = W[off + e];
@@ -73,7 +76,7 @@ __global__ void k_pack_mlp(const float* __restrict__ W, const float* __restrict_
   if (!fp8) {  // FP16 biases as MMA operands: W1 column 12, then [N x 16] tiles (column 0)
     int bo = 0;
     for (int l = 0; l < nl; ++l) {
-      const int o = l == nhid ? nout : kHid;
+      const int o = l == nhid ? nout : hid;
       for (int e = threadIdx.x; e < o; e += blockDim.x) {
         uint32_t dst;
         if (l == 0) dst = L.off_w1() + off_interleave(e, 2 * nin);
@@ -89,7 +92,7 @@ __global__ void k_pack_mlp(const float* __restrict__ W, const float* __restrict_
   float* alpha = reinterpret_cast<float*>(out + L.off_alpha());
   int boff = 0;
   for (int l = 0; l < nl; ++l) {
-    const int o = l == nhid ? nout : kHid;
+    const int o = l == nhid ? nout : hid;
     const float div = (fp8 && l < nhid) ? sa[l + 1] : 1.f;
     for (int e = threadIdx.x; e < o; e += blockDim.x) bias[l * kHid + e] = B[boff + e] / div;
     boff += o;
@@ -111,8 +114,10 @@ static nbtc_status tc_shape(const nbtc_mlp* mlp, int& nhid) {
   nhid = L - 1;
   if (nhid < 1 || nhid > 3) return fail(NBTC_ERR_UNSUPPORTED, "tensor-core forms take 1..3 hidden layers");
   if (mlp->dims[0] != 12) return fail(NBTC_ERR_UNSUPPORTED, "tensor-core forms take 12 input features");
+  const int D = mlp->dims[1];
+  if (D != 16 && D != 32 && D != kHid) return fail(NBTC_ERR_UNSUPPORTED, "tensor-core forms take hidden width 16, 32 or 64");
   for (int l = 1; l < L; ++l)
-    if (mlp->dims[l] != kHid) return fail(NBTC_ERR_UNSUPPORTED, "tensor-core forms take hidden width 64");
+    if (mlp->dims[l] != D) return fail(NBTC_ERR_UNSUPPORTED, "hidden layers must share one width");
   if (mlp->dims[L] < 1 || mlp->dims[L] > kMaxOut) return fail(NBTC_ERR_UNSUPPORTED, "at most 16 outputs");
   return NBTC_OK;
 }
@@ -135,8 +140,8 @@ nbtc_status launch_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int precisio
   if (packed_bytes < (size_t)L.bytes()) return fail(NBTC_ERR_INVALID_ARG, "packed buffer too small");
   if (!packed || !aligned(packed, 16)) return fail(NBTC_ERR_INVALID_ARG, "packed buffer NULL or not 16-byte aligned");
   if (L.fp8 && !act_absmax) return fail(NBTC_ERR_INVALID_ARG, "FP8 packing needs the calibration absmax");
-  k_pack_mlp<<<1, 256, 0, s>>>(mlp->weights, mlp->biases, nhid, mlp->dims[0], mlp->dims[nhid + 1], L.fp8 ? 1 : 0,
-                               act_absmax, static_cast<unsigned char*>(packed));
+  k_pack_mlp<<<1, 256, 0, s>>>(mlp->weights, mlp->biases, nhid, mlp->dims[0], mlp->dims[1], mlp->dims[nhid + 1],
+                               L.fp8 ? 1 : 0, act_absmax, static_cast<unsigned char*>(packed));
   return cuda_check(cudaGetLastError(), "launch k_pack_mlp");
 }
 

@@ -4,6 +4,7 @@
 
 #include "features.cuh"
 #include "host.h"
+#include "shade.cuh"
 
 namespace nbtc {
 
@@ -86,6 +87,8 @@ struct TcArgs {
   const float* flod;       // frame: per-pixel lod (log2 of the uv footprint + bias), or the bias with fduv
   const float* fduv;       // frame: per-pixel uv derivatives (anisotropic filter) or NULL
   int max_aniso;           // frame: probe cap of the anisotropic filter
+  float* fshade;           // frame: lighting pass output (FP32 RGBA per pixel) or NULL
+  LightDev light;          // frame: lighting constants
   uint16_t* fout;          // frame: per-pixel output (nout FP16)
   int frame_w, tile_w, tile_h, tiles_x;
 };

@@ -425,6 +425,13 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
 #pragma unroll
             for (int k = 0; k < kMaxOut; ++k)
               if (k < nout) o[k] = hv[k];
+            if (p.fshade) {  // lighting pass on the pixel's FP16 G-buffer channels
+              float y[8];
+#pragma unroll
+              for (int k = 0; k < 8; ++k) y[k] = __half2float(__ushort_as_half(hv[k]));
+              const float3 c = shade_pixel(y, p.light);
+              *reinterpret_cast<float4*>(p.fshade + 4 * px) = make_float4(c.x, c.y, c.z, 1.f);
+            }
           }
         }
       };

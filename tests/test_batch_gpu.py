@@ -146,6 +146,45 @@ def test_frame_anisotropic_filter_all_pixels(nb, ctx, max_aniso):
     plan.close()
 
 
+def test_frame_lighting_pass(nb, ctx):
+    """The fused lighting pass against the oracle's shading of the same FP16
+    G-buffer values the kernel produced.  FP32 vs FP64: the GGX term is the only
+    ill-conditioned one (near a sharp highlight a relative change e in n.h
+    changes D by about cond * e, cond = 4 (n.h)^2 (1 - a^2) / d), so the bound
+    is (256 + 16 cond) FP32 ulps of the pixel's largest channel."""
+    bw = synth.batch_workload(num_materials=4, frame_w=256, frame_h=128, smin=256, smax=512, seed=79)
+    bw.mat_id[np.random.default_rng(2).random(bw.mat_id.shape) < 0.02] = -1
+    mats = [nb.Material.from_synth(m) for m in bw.materials]
+    fr = _frame_tensors(bw)
+    shaded = torch.full((bw.frame_h, bw.frame_w, 4), float("nan"), dtype=torch.float32, device="cuda")
+    light = {"light_dir": (0.3, -0.5, 0.8), "light_rgb": (3.0, 2.5, 2.0), "view_dir": (0.1, 0.2, 1.0),
+             "sky": (0.5, 0.6, 0.9), "ground": (0.2, 0.15, 0.1)}
+    fr["shaded"], fr["light"] = shaded, light
+    plan = nb.Batch(ctx, mats, None, fr, autotune=False)
+    plan.render()
+    ctx.sync()
+    ids = bw.mat_id.reshape(-1)
+    y = fr["out"].view(-1, 9).float().cpu().numpy().astype(np.float64)[ids >= 0]
+    got = shaded.view(-1, 4).cpu().numpy().astype(np.float64)
+    assert np.all(np.isnan(got[ids < 0]))           # pixels without a material are left untouched
+    got = got[ids >= 0]
+    ref = oracle.shade.shade(y, light["light_dir"], light["light_rgb"], light["view_dir"], light["sky"], light["ground"])
+    albedo, n, rough, metal, ao = oracle.shade.surface(y)
+    l = np.array(light["light_dir"]) / np.linalg.norm(light["light_dir"])
+    v = np.array(light["view_dir"]) / np.linalg.norm(light["view_dir"])
+    h = (l + v) / np.linalg.norm(l + v)
+    a2 = rough ** 4
+    x = np.maximum(n @ h, 0.0)
+    dd = x * x * (a2 - 1.0) + 1.0
+    cond = 4.0 * x * x * (1.0 - a2) / dd
+    bound = (256.0 + 16.0 * cond) * 2.0 ** -24 * np.abs(ref).max(axis=1) + 1e-6
+    err = np.abs(got[:, :3] - ref).max(axis=1)
+    assert np.all(err <= bound), float((err / bound).max())
+    assert np.all(got[:, 3] == 1.0)
+    assert np.isfinite(got).all()
+    plan.close()
+
+
 def test_full_size_batch(nb, ctx):
     """64 materials of 256^2..4096^2 and a 3840x2160 frame, as the benchmark runs
     them: sampled texels of every material and 20,000 frame pixels."""

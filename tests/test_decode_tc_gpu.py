@@ -165,7 +165,21 @@ def _fp8_setup(nb, ctx, wl, gw, gh):
     return mat, packed, (sw, sa)
 
 
-@pytest.mark.parametrize("dims", [[12, 64, 9], [12, 64, 64, 64, 9]])
+@pytest.mark.parametrize("dims,layout", [([12, 16, 9], "B"), ([12, 32, 9], "A"), ([12, 32, 32, 9], "B"),
+                                         ([12, 16, 9], "A"), ([12, 64, 9], "A")])
+def test_fp16_hidden_width_sweep(nb, ctx, dims, layout):
+    """Table 1's one-hidden-layer MLPs of width D = 16 / 32 / 64 (zero-padded to
+    the 64-wide image) on the paper's latent layouts: variant B (1/4, 1/8, 1/16,
+    1/32 of the output side) and variant A (1/4, 1/4, 1/8, 1/8)."""
+    side = 512
+    lv = [side // 4, side // 8, side // 16, side // 32] if layout == "B" else [side // 4, side // 4, side // 8, side // 8]
+    wl = synth.small_decode_workload(side, dims, seed=340 + dims[1] + len(dims), level_sides=lv)
+    got = _fp16_case(nb, ctx, wl, grid=(side, 96))
+    emu = oracle.decode.decode_grid(wl.material, side, 96, precision="fp16")
+    _check_fp16(got, emu, wl.material, _grid_x(wl.material, side, 96))
+
+
+@pytest.mark.parametrize("dims", [[12, 64, 9], [12, 64, 64, 64, 9], [12, 32, 9]])
 def test_fp8_grid(nb, ctx, dims):
     wl = synth.small_decode_workload(512, dims, seed=330 + len(dims))
     mat, packed, scales = _fp8_setup(nb, ctx, wl, 512, 128)
@@ -191,6 +205,13 @@ def test_packed_sizes(nb, ctx):
     mat = nb.Material.from_synth(wl.material)
     assert api.packed_mlp_bytes(mat, nb.FP16) % 16 == 0
     assert api.packed_mlp_bytes(mat, nb.FP8_E4M3) < api.packed_mlp_bytes(mat, nb.FP16)
-    wl0 = synth.decode_workload(0)   # hidden width 32: no tensor-core kernel
+    # hidden width 32 packs zero-padded into the same 64-wide image
+    wl0 = synth.decode_workload(0)
+    m32 = nb.Material.from_synth(synth.small_decode_workload(256, [12, 32, 32, 9], seed=5).material)
+    assert api.packed_mlp_bytes(m32, nb.FP16) == api.packed_mlp_bytes(
+        nb.Material.from_synth(synth.small_decode_workload(256, [12, 64, 64, 9], seed=5).material), nb.FP16)
+    assert api.packed_mlp_bytes(nb.Material.from_synth(wl0.material), nb.FP16) > 0
+    # other widths have no tensor-core kernel
     with pytest.raises(nb.NbtcError):
-        api.packed_mlp_bytes(nb.Material.from_synth(wl0.material), nb.FP16)
+        api.packed_mlp_bytes(nb.Material.from_synth(synth.small_decode_workload(256, [12, 48, 9], seed=5).material),
+                             nb.FP16)
