@@ -337,12 +337,19 @@ def run_batch(args, nb, ctx, stream, flush) -> dict:
     ta = _time_steps(lambda: aplan.render(stream), max(3, args.steps // 4), args.warmup, flush, stream)
     ctx.sync(stream)
     aplan.close()
+    # the frame with the lighting pass fused into its epilogue (trilinear latents)
+    fl = dict(fr, shaded=torch.empty((bw.frame_h, bw.frame_w, 4), dtype=torch.float32, device="cuda"))
+    lplan = nb.Batch(ctx, mats, None, fl, autotune=True, stream=stream)
+    tl = _time_steps(lambda: lplan.render(stream), max(3, args.steps // 4), args.warmup, flush, stream)
+    ctx.sync(stream)
+    lplan.close()
     pixels = bw.frame_w * bw.frame_h
     return {"workload": bw.name, "materials": len(bw.materials), "decode_texels": texels,
             "decode_gtexel_s": texels / statistics.mean(td) / 1e6, "decode_ms": statistics.mean(td),
             "frame": f"{bw.frame_w}x{bw.frame_h}", "frame_ms": statistics.mean(tr),
             "frame_gpx_s": pixels / statistics.mean(tr) / 1e6, "plan": info,
-            "frame_aniso16_ms": statistics.mean(ta), "frame_aniso16_gpx_s": pixels / statistics.mean(ta) / 1e6}
+            "frame_aniso16_ms": statistics.mean(ta), "frame_aniso16_gpx_s": pixels / statistics.mean(ta) / 1e6,
+            "frame_lit_ms": statistics.mean(tl), "frame_lit_gpx_s": pixels / statistics.mean(tl) / 1e6}
 
 
 def run_ours(args) -> dict | None:
