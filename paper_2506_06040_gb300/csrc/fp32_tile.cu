@@ -1,12 +1,14 @@
-// FP32 SIMT form of the fused decode as a tiled GEMM (hidden width 64).
+// FP32 SIMT form of the fused decode as a tiled GEMM (hidden width D = 16, 32
+// or 64).
 //
 // A CTA of 256 threads decodes tiles of 256 consecutive output texels of one
 // row: the footprint feature stage (features.cuh) writes the 12 features of the
 // tile feature-major into shared memory, then every layer is a register-blocked
-// FP32 GEMM over the tile -- each thread owns 8 texels x 8 neurons (64 FFMA per
-// k step from two 128-bit activation loads and two broadcast 128-bit weight
-// loads), hidden activations are rewritten in place between layers, and the
-// output layer's rows are staged for coalesced 128-bit stores.  True FP32 FFMA
+// FP32 GEMM over the tile -- each thread owns D / 8 texels x 8 neurons (at
+// D = 64: 64 FFMA per k step from two 128-bit activation loads and two
+// broadcast 128-bit weight loads), hidden activations are rewritten in place
+// between layers, and the output layer's rows are staged for coalesced 128-bit
+// stores.  True FP32 FFMA
 // throughout (the plain FP32 form of the method, Sec. 5 "software FMA").
 #include "features.cuh"
 #include "host.h"
@@ -16,96 +18,128 @@ namespace nbtc {
 namespace {
 
 constexpr int kT = 256;      // texels per tile = threads per CTA
-constexpr int kD = 64;       // hidden width
 constexpr int kIn = 12;
 constexpr int kOutMax = 16;
 
-template <int NHID>
+template <int D, int NHID>
 struct TileSmem {
-  float w1t[kIn * kD];                 // [k][n]
-  float wht[(NHID - 1) * kD * kD];     // hidden->hidden, [k][n] per layer (NHID-1 >= 0)
-  float wot[kD * kOutMax];             // [k][c]
-  float b[NHID * kD + kOutMax];
-  float x[kOutMax * kT];               // features [k][texel]; reused as output staging [texel][c]
-  float h[kD * kT];                    // activations [n][texel]; reused as the column buffer
+  float w1t[kIn * D];                       // [k][n]
+  float wht[(NHID > 1 ? NHID - 1 : 1) * D * D];  // hidden->hidden, [k][n] per layer
+  float wot[D * kOutMax];                   // [k][c]
+  float b[NHID * D + kOutMax];
+  float x[kOutMax * kT];                    // features [k][texel]; reused as output staging [texel][c]
+  float h[D * kT];                          // activations [n][texel]; also the column buffer
 };
+static_assert(16 * kT >= 4 * kColCap * 4, "the column buffer fits the smallest activation buffer");
 
-// Thread (sg, ng) owns texels 4 sg + {0..3} and 128 + 4 sg + {0..3} (so each
-// 128-bit activation load is contiguous across the warp: no bank conflicts)
-// and neurons 8 ng + {0..7}.  Accumulators are texel pairs (FP32x2): acc[i][j]
-// holds texels (2i, 2i+1) of the thread's 8 for neuron 8 ng + j, so every
-// multiply-add is one packed FMA (two IEEE FP32 FMAs) and a weight feeds two
-// texels per instruction.
-template <int K>
-__device__ __forceinline__ void gemm8x8(const float* __restrict__ A, const float* __restrict__ Bt, int sg, int ng,
-                                        float2 (&acc)[4][8]) {
+// Thread (sg, ng) owns neurons 8 ng + {0..7} and TPT = D / 8 texels of the
+// tile, laid out so each activation load is contiguous across the warp (no
+// bank conflicts): TPT = 8 -> texels 4 sg + {0..3} and 128 + 4 sg + {0..3};
+// TPT = 4 -> 4 sg + {0..3}; TPT = 2 -> 2 sg + {0, 1}.  Accumulators are texel
+// pairs (FP32x2): acc[i][j] holds texels (2i, 2i+1) of the thread's TPT for
+// neuron 8 ng + j, so every multiply-add is one packed FMA (two IEEE FP32 FMAs)
+// and a weight feeds two texels per instruction.
+template <int TPT>
+__device__ __forceinline__ void load_pairs(const float* __restrict__ row, int sg, float2 (&av)[TPT / 2]) {
+  if constexpr (TPT == 8) {
+    const float4 a0 = *reinterpret_cast<const float4*>(row + 4 * sg);
+    const float4 a1 = *reinterpret_cast<const float4*>(row + kT / 2 + 4 * sg);
+    av[0] = make_float2(a0.x, a0.y);
+    av[1] = make_float2(a0.z, a0.w);
+    av[2] = make_float2(a1.x, a1.y);
+    av[3] = make_float2(a1.z, a1.w);
+  } else if constexpr (TPT == 4) {
+    const float4 a0 = *reinterpret_cast<const float4*>(row + 4 * sg);
+    av[0] = make_float2(a0.x, a0.y);
+    av[1] = make_float2(a0.z, a0.w);
+  } else {
+    av[0] = *reinterpret_cast<const float2*>(row + 2 * sg);
+  }
+}
+
+template <int TPT>
+__device__ __forceinline__ void store_pairs(float* __restrict__ row, int sg, const float2 (&v)[TPT / 2]) {
+  if constexpr (TPT == 8) {
+    *reinterpret_cast<float4*>(row + 4 * sg) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    *reinterpret_cast<float4*>(row + kT / 2 + 4 * sg) = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+  } else if constexpr (TPT == 4) {
+    *reinterpret_cast<float4*>(row + 4 * sg) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  } else {
+    *reinterpret_cast<float2*>(row + 2 * sg) = v[0];
+  }
+}
+
+template <int K, int D, int TPT>
+__device__ __forceinline__ void gemm_block(const float* __restrict__ A, const float* __restrict__ Bt, int sg, int ng,
+                                           float2 (&acc)[TPT / 2][8]) {
 #pragma unroll 2
   for (int k = 0; k < K; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kT + 4 * sg);
-    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kT + kT / 2 + 4 * sg);
-    const float4 b0 = *reinterpret_cast<const float4*>(Bt + k * kD + 8 * ng);
-    const float4 b1 = *reinterpret_cast<const float4*>(Bt + k * kD + 8 * ng + 4);
-    const float2 av[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
-                          make_float2(a1.z, a1.w)};
+    float2 av[TPT / 2];
+    load_pairs<TPT>(A + k * kT, sg, av);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bt + k * D + 8 * ng);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bt + k * D + 8 * ng + 4);
     const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const float2 w = make_float2(bv[j], bv[j]);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) acc[i][j] = __ffma2_rn(av[i], w, acc[i][j]);
+      for (int i = 0; i < TPT / 2; ++i) acc[i][j] = __ffma2_rn(av[i], w, acc[i][j]);
     }
   }
 }
 
-__device__ __forceinline__ void init_bias(const float* __restrict__ b, int ng, float2 (&acc)[4][8]) {
+template <int TPT>
+__device__ __forceinline__ void init_bias(const float* __restrict__ b, int ng, float2 (&acc)[TPT / 2][8]) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const float v = b[8 * ng + j];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i][j] = make_float2(v, v);
+    for (int i = 0; i < TPT / 2; ++i) acc[i][j] = make_float2(v, v);
   }
 }
 
-__device__ __forceinline__ void store_relu(float* __restrict__ H, int sg, int ng, const float2 (&acc)[4][8]) {
+template <int TPT>
+__device__ __forceinline__ void store_relu(float* __restrict__ H, int sg, int ng, const float2 (&acc)[TPT / 2][8]) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    float* row = H + (8 * ng + j) * kT;
-    *reinterpret_cast<float4*>(row + 4 * sg) = make_float4(fmaxf(acc[0][j].x, 0.f), fmaxf(acc[0][j].y, 0.f),
-                                                           fmaxf(acc[1][j].x, 0.f), fmaxf(acc[1][j].y, 0.f));
-    *reinterpret_cast<float4*>(row + kT / 2 + 4 * sg) = make_float4(fmaxf(acc[2][j].x, 0.f), fmaxf(acc[2][j].y, 0.f),
-                                                                    fmaxf(acc[3][j].x, 0.f), fmaxf(acc[3][j].y, 0.f));
+    float2 v[TPT / 2];
+#pragma unroll
+    for (int i = 0; i < TPT / 2; ++i) v[i] = make_float2(fmaxf(acc[i][j].x, 0.f), fmaxf(acc[i][j].y, 0.f));
+    store_pairs<TPT>(H + (8 * ng + j) * kT, sg, v);
   }
 }
 
-template <int NHID, int NO>
+template <int D, int NHID, int NO>
 __global__ void __launch_bounds__(kT, 2) k_decode_fp32_tile(DecodeArgs a, const float* __restrict__ gW,
                                                            const float* __restrict__ gB, int nout, int footprint) {
+  constexpr int TPT = D / 8;           // texels per thread
+  constexpr int TG = kT / TPT;         // texel groups = threads per neuron group
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem<NHID>& S = *reinterpret_cast<TileSmem<NHID>*>(smem_raw);
+  TileSmem<D, NHID>& S = *reinterpret_cast<TileSmem<D, NHID>*>(smem_raw);
   const int t = threadIdx.x;
   // ---- weights: global [out][in] per layer -> shared [in][out]
   {
     int off = 0;
-    for (int e = t; e < kD * kIn; e += kT) {
+    for (int e = t; e < D * kIn; e += kT) {
       const int n = e / kIn, k = e - n * kIn;
-      S.w1t[k * kD + n] = gW[e];
+      S.w1t[k * D + n] = gW[e];
     }
-    off += kD * kIn;
+    off += D * kIn;
     for (int l = 0; l < NHID - 1; ++l) {
-      for (int e = t; e < kD * kD; e += kT) {
-        const int n = e / kD, k = e - n * kD;
-        S.wht[l * kD * kD + k * kD + n] = gW[off + e];
+      for (int e = t; e < D * D; e += kT) {
+        const int n = e / D, k = e - n * D;
+        S.wht[l * D * D + k * D + n] = gW[off + e];
       }
-      off += kD * kD;
+      off += D * D;
     }
-    for (int e = t; e < kD * kOutMax; e += kT) {
-      const int c = e / kD, k = e - c * kD;
-      S.wot[k * kOutMax + c] = c < nout ? gW[off + c * kD + k] : 0.f;
+    for (int e = t; e < D * kOutMax; e += kT) {
+      const int c = e / D, k = e - c * D;
+      S.wot[k * kOutMax + c] = c < nout ? gW[off + c * D + k] : 0.f;
     }
-    for (int e = t; e < NHID * kD + kOutMax; e += kT) S.b[e] = e < NHID * kD + nout ? gB[e] : 0.f;
+    for (int e = t; e < NHID * D + kOutMax; e += kT) S.b[e] = e < NHID * D + nout ? gB[e] : 0.f;
   }
   __syncthreads();
-  const int sg = t & 31, ng = t >> 5;  // warp = 8-neuron group (weights broadcast), lane = 8-texel group
+  const int sg = t % TG, ng = t / TG;  // warp-uniform neuron group (weights broadcast), lane = texel group
   const int64_t tiles = (a.n + kT - 1) / kT;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t t0 = tile * kT;
@@ -122,29 +156,29 @@ __global__ void __launch_bounds__(kT, 2) k_decode_fp32_tile(DecodeArgs a, const 
     __syncthreads();
     // ---- layer 1
     {
-      float2 acc[4][8];
-      init_bias(S.b, ng, acc);
-      gemm8x8<kIn>(S.x, S.w1t, sg, ng, acc);
-      store_relu(S.h, sg, ng, acc);
+      float2 acc[TPT / 2][8];
+      init_bias<TPT>(S.b, ng, acc);
+      gemm_block<kIn, D, TPT>(S.x, S.w1t, sg, ng, acc);
+      store_relu<TPT>(S.h, sg, ng, acc);
     }
     __syncthreads();
     // ---- hidden layers, in place
 #pragma unroll 1
     for (int l = 0; l < NHID - 1; ++l) {
-      float2 acc[4][8];
-      init_bias(S.b + (l + 1) * kD, ng, acc);
-      gemm8x8<kD>(S.h, S.wht + l * kD * kD, sg, ng, acc);
+      float2 acc[TPT / 2][8];
+      init_bias<TPT>(S.b + (l + 1) * D, ng, acc);
+      gemm_block<D, D, TPT>(S.h, S.wht + l * D * D, sg, ng, acc);
       __syncthreads();
-      store_relu(S.h, sg, ng, acc);
+      store_relu<TPT>(S.h, sg, ng, acc);
       __syncthreads();
     }
     // ---- output layer: thread t -> texel t, NO (padded) channels as FP32x2 pairs; staged in x
     {
       float2 y[NO / 2];
 #pragma unroll
-      for (int c = 0; c < NO / 2; ++c) y[c] = make_float2(S.b[NHID * kD + 2 * c], S.b[NHID * kD + 2 * c + 1]);
+      for (int c = 0; c < NO / 2; ++c) y[c] = make_float2(S.b[NHID * D + 2 * c], S.b[NHID * D + 2 * c + 1]);
 #pragma unroll 4
-      for (int k = 0; k < kD; ++k) {
+      for (int k = 0; k < D; ++k) {
         const float hv = S.h[k * kT + t];
         const float2 h2 = make_float2(hv, hv);
         const float2* w = reinterpret_cast<const float2*>(S.wot + k * kOutMax);
@@ -174,10 +208,10 @@ __global__ void __launch_bounds__(kT, 2) k_decode_fp32_tile(DecodeArgs a, const 
   }
 }
 
-template <int NHID>
+template <int D, int NHID>
 nbtc_status launch_tile(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, int footprint, cudaStream_t s) {
-  const size_t smem = sizeof(TileSmem<NHID>);
-  auto kern = mlp->dims[mlp->num_layers] <= 10 ? k_decode_fp32_tile<NHID, 10> : k_decode_fp32_tile<NHID, 16>;
+  const size_t smem = sizeof(TileSmem<D, NHID>);
+  auto kern = mlp->dims[mlp->num_layers] <= 10 ? k_decode_fp32_tile<D, NHID, 10> : k_decode_fp32_tile<D, NHID, 16>;
   nbtc_status st =
       cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
   if (st) return st;
@@ -193,21 +227,32 @@ nbtc_status launch_tile(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* 
 
 }  // namespace
 
-// Tiled FP32 decode for MLPs [12, 64, .., 64, C <= 16] (1-3 hidden layers);
-// returns NBTC_ERR_UNSUPPORTED (without launching) for other shapes.
+// Tiled FP32 decode for MLPs [12, D, .., D, C <= 16] with D in {16, 32, 64}
+// and 1-3 hidden layers; returns NBTC_ERR_UNSUPPORTED (without launching) for
+// other shapes.
 nbtc_status launch_decode_fp32_tile(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, cudaStream_t s) {
   const int L = mlp->num_layers;
+  const int D = mlp->dims[1];
   if (mlp->dims[0] != kIn || L < 2 || L > 4 || mlp->dims[L] > kOutMax) return NBTC_ERR_UNSUPPORTED;
+  if (D != 16 && D != 32 && D != 64) return NBTC_ERR_UNSUPPORTED;
   for (int l = 1; l < L; ++l)
-    if (mlp->dims[l] != kD) return NBTC_ERR_UNSUPPORTED;
+    if (mlp->dims[l] != D) return NBTC_ERR_UNSUPPORTED;
   // footprint stage: tiles inside one output row, every level's span within the column buffer
   bool fp = a.uv == nullptr && (a.grid_w % kT) == 0;
   for (int k = 0; k < 4; ++k) fp = fp && (int64_t)(kT - 1) * a.lv[k].w / a.grid_w + 3 <= kColCap;
-  switch (L - 1) {
-    case 1: return launch_tile<1>(ctx, a, mlp, fp, s);
-    case 2: return launch_tile<2>(ctx, a, mlp, fp, s);
-    default: return launch_tile<3>(ctx, a, mlp, fp, s);
+#define NBTC_TILE(DD)                                           \
+  if (D == DD) {                                                \
+    switch (L - 1) {                                            \
+      case 1: return launch_tile<DD, 1>(ctx, a, mlp, fp, s);    \
+      case 2: return launch_tile<DD, 2>(ctx, a, mlp, fp, s);    \
+      default: return launch_tile<DD, 3>(ctx, a, mlp, fp, s);   \
+    }                                                           \
   }
+  NBTC_TILE(16)
+  NBTC_TILE(32)
+  NBTC_TILE(64)
+#undef NBTC_TILE
+  return NBTC_ERR_UNSUPPORTED;
 }
 
 }  // namespace nbtc
