@@ -2,14 +2,16 @@
 // (bilinear latent sampling + MLP 12-64-64-C), loss against the bilinearly
 // sampled target, backward through the MLP into every latent texel, Adam.
 //
-// k_train: persistent CTAs of 256 threads walk 64-sample tiles.  Per tile all
-// activations live in shared memory, feature-major ([k][sample], samples
-// contiguous), and every dense product is a register-blocked SIMT FP32 GEMM
-// (true FP32 FFMA; activations are recomputed per call, never stored to HBM).
-// Weight/bias gradients: per-tile sums added into per-CTA running sums with
-// Neumaier compensation, written to the workspace at the end; k_reduce_adam
-// adds the CTA partials in a fixed order (compensated), writes the gradients
-// and applies Adam.  Latent gradients: FP32 atomics (red.global.add).
+// k_train: persistent CTAs of 256 threads (one per SM) walk 256-sample tiles.
+// Per tile all activations live in shared memory, feature-major ([k][sample],
+// samples contiguous; backward deltas overwrite the activations they follow),
+// and every dense product is a register-blocked SIMT FP32 GEMM on packed FP32x2
+// FMAs (true FP32 FFMA; activations are recomputed per call, never stored to
+// HBM).  Weight/bias gradients: per-tile sums added into per-thread running
+// sums with Neumaier compensation (each thread owns fixed entries), written to
+// the workspace at the end; k_reduce_adam adds the CTA partials in a fixed
+// order (compensated), writes the gradients and applies Adam.  Latent
+// gradients: FP32 atomics (red.global.add).
 #include <mutex>
 #include <string>
 
@@ -17,12 +19,12 @@
 
 namespace nbtc {
 
-constexpr int kTS = 64;         // samples per tile
+constexpr int kTS = 256;        // samples per tile
+constexpr int kLd = kTS + 4;    // row stride of the activations: consecutive rows 4 banks apart
 constexpr int kTT = 256;        // threads per CTA
 constexpr int kH = 64;          // hidden width
 constexpr int kIn = 12;         // features
 constexpr int kCMax = 16;       // output channels (padded)
-constexpr int kLd = kTS + 4;    // row stride of feature-major activations (16-byte rows, bank shift 4)
 
 // gradient slots: dW1 [64][12], dW2 [64][64], dW3 [16][64], db1, db2, db3 (padded C)
 constexpr int kGW1 = 0, kGW2 = kGW1 + kH * kIn, kGW3 = kGW2 + kH * kH, kGB1 = kGW3 + kCMax * kH,
@@ -83,37 +85,97 @@ __device__ __forceinline__ Taps clamp_taps(float u, float v, int w, int h, float
   return t;
 }
 
+// Shared memory of k_train: weights in both orientations (forward products
+// read W^T rows, backward products read W rows, both as broadcast 128-bit
+// loads), biases, and the tile's activations feature-major [row][sample]:
+// X (features), H1, H2 (later overwritten by D1, D2), DY (targets, then dL/dy).
 struct TrainSmem {
-  float W1[kH * kIn], W1t[kIn * kH], W2[kH * kH], W2t[kH * kH], W3[kCMax * kH], W3t[kH * kCMax];
+  float W1t[kIn * kH], W1[kH * kIn], W2t[kH * kH], W2[kH * kH], W3t[kH * kCMax], W3[kCMax * kH];
   float b1[kH], b2[kH], b3[kCMax];
-  float X[kIn * kLd], H1[kH * kLd], H2[kH * kLd], D2[kH * kLd], D1[kH * kLd], DY[kCMax * kLd];
-  float gs[kGN], ge[kGN];  // running gradient sums (sum, compensation), owned per thread
+  float X[kIn * kLd], H1[kH * kLd], H2[kH * kLd], DY[kCMax * kLd];
   float red[2 * (kTT / 32)];
 };
 
-// [64 samples x 64 outputs] = A^T-products over K: acc[i][j] for samples 4sg+i,
-// outputs 4ng+j, A feature-major [K][kLd], B [K][64] row-major.
+// Thread (sg, ng) of a [256 samples x 64 outputs] product owns outputs 8 ng +
+// {0..7} and samples 4 sg + {0..3}, 128 + 4 sg + {0..3} (each activation load
+// contiguous across the warp); accumulators are sample pairs, one packed FMA
+// (two IEEE FP32 FMAs) per weight and pair.
+__device__ __forceinline__ void load_samples(const float* __restrict__ row, int sg, float2 (&av)[4]) {
+  const float4 a0 = *reinterpret_cast<const float4*>(row + 4 * sg);
+  const float4 a1 = *reinterpret_cast<const float4*>(row + kTS / 2 + 4 * sg);
+  av[0] = make_float2(a0.x, a0.y);
+  av[1] = make_float2(a0.z, a0.w);
+  av[2] = make_float2(a1.x, a1.y);
+  av[3] = make_float2(a1.z, a1.w);
+}
+
+// acc[i][j] += sum_k A[k][samples i] * Bm[k][8 ng + j], Bm rows of kH floats
 template <int K>
-__device__ __forceinline__ void gemm_4x4(const float* __restrict__ A, const float* __restrict__ Bm, int sg, int ng,
-                                         float (&acc)[4][4]) {
-#pragma unroll 4
+__device__ __forceinline__ void gemm_8x8(const float* __restrict__ A, const float* __restrict__ Bm, int sg, int ng,
+                                         float2 (&acc)[4][8]) {
+#pragma unroll 2
   for (int k = 0; k < K; ++k) {
-    const float4 a = *reinterpret_cast<const float4*>(A + k * kLd + 4 * sg);
-    const float4 b = *reinterpret_cast<const float4*>(Bm + k * kH + 4 * ng);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    float2 av[4];
+    load_samples(A + k * kLd, sg, av);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bm + k * kH + 8 * ng);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bm + k * kH + 8 * ng + 4);
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 8; ++j) {
+      const float2 w = make_float2(bv[j], bv[j]);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int i = 0; i < 4; ++i) acc[i][j] = __ffma2_rn(av[i], w, acc[i][j]);
+    }
   }
 }
 
-__device__ __forceinline__ void store_4x4(float* __restrict__ Out, int sg, int ng, const float (&acc)[4][4]) {
+__device__ __forceinline__ void store_8x8(float* __restrict__ Out, int sg, int ng, const float2 (&v)[4][8]) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    *reinterpret_cast<float4*>(Out + (4 * ng + j) * kLd + 4 * sg) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+  for (int j = 0; j < 8; ++j) {
+    float* row = Out + (8 * ng + j) * kLd;
+    *reinterpret_cast<float4*>(row + 4 * sg) = make_float4(v[0][j].x, v[0][j].y, v[1][j].x, v[1][j].y);
+    *reinterpret_cast<float4*>(row + kTS / 2 + 4 * sg) = make_float4(v[2][j].x, v[2][j].y, v[3][j].x, v[3][j].y);
+  }
 }
 
+// acc[j] = (sum over the tile's samples of A[ra + ...] * B[rb + ...]) for a
+// thread's outputs: the sums along samples, 4 at a time (128-bit loads), even
+// and odd samples in the two halves of a packed accumulator.
+template <int NA, int NB>
+__device__ __forceinline__ void sample_dots(const float* __restrict__ A, const int (&ra)[NA],
+                                            const float* __restrict__ B, const int (&rb)[NB], float (&out)[NA][NB]) {
+  float2 acc[NA][NB];
+#pragma unroll
+  for (int i = 0; i < NA; ++i)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int s = 0; s < kTS; s += 4) {
+    float4 av[NA], bv[NB];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) av[i] = *reinterpret_cast<const float4*>(A + ra[i] * kLd + s);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) bv[j] = *reinterpret_cast<const float4*>(B + rb[j] * kLd + s);
+#pragma unroll
+    for (int i = 0; i < NA; ++i)
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        acc[i][j] = __ffma2_rn(make_float2(av[i].x, av[i].y), make_float2(bv[j].x, bv[j].y), acc[i][j]);
+        acc[i][j] = __ffma2_rn(make_float2(av[i].z, av[i].w), make_float2(bv[j].z, bv[j].w), acc[i][j]);
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < NA; ++i)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) out[i][j] = acc[i][j].x + acc[i][j].y;
+}
+
+// k_train: persistent CTAs of 256 threads (one per SM) walk 256-sample tiles.
+// Per tile: features and targets (thread = sample), H1, H2, outputs and dL/dy,
+// then dW3 / D2, dW2 / D1, dW1 and the latent scatter.  Every thread keeps the
+// running (Neumaier) sums of the weight-gradient entries it computes in
+// registers across tiles -- the same entries every tile -- and writes them to
+// the CTA's partial slots at the end.
 template <int MODE>
 __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -143,99 +205,118 @@ __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
     S.b2[e] = a.B[kH + e];
   }
   if (t < kCMax) S.b3[t] = t < C ? a.B[2 * kH + t] : 0.f;
-  for (int e = t; e < kGN; e += kTT) S.gs[e] = S.ge[e] = 0.f;
   for (int e = t; e < kCMax * kLd; e += kTT) S.DY[e] = 0.f;
   __syncthreads();
 
-  const int sg = t & 15, ng = t >> 4;  // GEMM blocking: samples 4sg.., outputs 4ng..
-  const int ts = t & 63, tp = t >> 6;  // per-sample work: sample ts, part tp (0..3)
+  const int sg = t & 31, ng = t >> 5;  // product blocking (warp = output group)
+  // Weight-gradient entries owned by this thread (the same every tile), chosen
+  // so the rows a warp reads at one sample offset sit in distinct banks:
+  //   dW2: rows w2o + 4p x cols w2i + 8q (p, q = 0..3), w2o = 16 (warp & 3) + (lane >> 3),
+  //        w2i = 32 (warp >> 2) + (lane & 7)
+  //   dW3: row 4 (warp & 3) + (lane >> 3) x cols w2i + 8q
+  //   dW1: row 8 warp + (lane >> 2) x cols (lane & 3) + 4q (q = 0..2)
+  //   biases: db1 (t < 64), db2 (64 <= t < 128), db3 (128 <= t < 144)
+  const int lane = t & 31, warp = t >> 5;
+  const int w2o = 16 * (warp & 3) + (lane >> 3), w2i = 32 * (warp >> 2) + (lane & 7);
+  const int w3c = 4 * (warp & 3) + (lane >> 3);
+  const int w1o = 8 * warp + (lane >> 2), w1i = lane & 3;
+  float g2s[4][4] = {}, g2e[4][4] = {}, g1s[3] = {}, g1e[3] = {}, g3s[4] = {}, g3e[4] = {}, gbs = 0.f, gbe = 0.f;
   float loss_s = 0.f, loss_e = 0.f;
   const int64_t ntiles = (a.batch + kTS - 1) / kTS;
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t s0 = tile * kTS;
-    const int64_t sid = s0 + ts;
+    const int64_t sid = tile * kTS + t;
     const bool valid = sid < a.batch;
     const float2 uv = valid ? __ldg(reinterpret_cast<const float2*>(a.uv) + sid) : make_float2(0.f, 0.f);
-    // ---- features: part tp = latent level tp
-    {
-      const Taps T = clamp_taps(uv.x, uv.y, a.lw[tp], a.lh[tp], a.shift[tp]);
-      const float* L = a.lat[tp];
+    // ---- features (thread = sample): 4 levels x 3 channels
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
+      const float* L = a.lat[k];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float f = T.w00 * __ldg(L + 3 * T.i00 + c) + T.w10 * __ldg(L + 3 * T.i10 + c) +
                         T.w01 * __ldg(L + 3 * T.i01 + c) + T.w11 * __ldg(L + 3 * T.i11 + c);
-        S.X[(3 * tp + c) * kLd + ts] = valid ? f : 0.f;
+        S.X[(3 * k + c) * kLd + t] = valid ? f : 0.f;
       }
     }
-    // ---- targets (train mode), channels tp, tp+4, ...  -> DY rows (turned into dY below)
+    // ---- targets (train mode) -> DY rows (turned into dL/dy below)
     if (MODE == kModeTrain) {
       const Taps T = clamp_taps(uv.x, uv.y, a.tw, a.th, 0.f);
-      for (int c = tp; c < C; c += 4) {
+      for (int c = 0; c < C; ++c) {
         const float v = T.w00 * __ldg(a.target + (size_t)T.i00 * C + c) + T.w10 * __ldg(a.target + (size_t)T.i10 * C + c) +
                         T.w01 * __ldg(a.target + (size_t)T.i01 * C + c) + T.w11 * __ldg(a.target + (size_t)T.i11 * C + c);
-        S.DY[c * kLd + ts] = v;
+        S.DY[c * kLd + t] = v;
       }
     }
     __syncthreads();
-    // ---- H1 = ReLU(W1 x + b1)
+    // ---- H1 = ReLU(W1 x + b1), H2 = ReLU(W2 h1 + b2)
     {
-      float acc[4][4];
+      float2 acc[4][8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float b = S.b1[8 * ng + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i][j] = make_float2(b, b);
+      }
+      gemm_8x8<kIn>(S.X, S.W1t, sg, ng, acc);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = S.b1[4 * ng + j];
-      gemm_4x4<kIn>(S.X, S.W1t, sg, ng, acc);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaxf(acc[i][j], 0.f);
-      store_4x4(S.H1, sg, ng, acc);
+        for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(fmaxf(acc[i][j].x, 0.f), fmaxf(acc[i][j].y, 0.f));
+      store_8x8(S.H1, sg, ng, acc);
     }
     __syncthreads();
-    // ---- H2 = ReLU(W2 h1 + b2)
     {
-      float acc[4][4];
+      float2 acc[4][8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float b = S.b2[8 * ng + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i][j] = make_float2(b, b);
+      }
+      gemm_8x8<kH>(S.H1, S.W2t, sg, ng, acc);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = S.b2[4 * ng + j];
-      gemm_4x4<kH>(S.H1, S.W2t, sg, ng, acc);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaxf(acc[i][j], 0.f);
-      store_4x4(S.H2, sg, ng, acc);
+        for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(fmaxf(acc[i][j].x, 0.f), fmaxf(acc[i][j].y, 0.f));
+      store_8x8(S.H2, sg, ng, acc);
     }
     __syncthreads();
-    // ---- y = W3 h2 + b3 (channels tp, tp+4, ...), then dL/dy
+    // ---- y = W3 h2 + b3 (thread = sample), loss and dL/dy -> DY
     {
-      float y[4];
+      float y[kCMax];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) y[q] = S.b3[tp + 4 * q];
-#pragma unroll 8
+      for (int c = 0; c < kCMax; ++c) y[c] = S.b3[c];
+#pragma unroll 4
       for (int k = 0; k < kH; ++k) {
-        const float h = S.H2[k * kLd + ts];
+        const float h = S.H2[k * kLd + t];
+        const float4* w = reinterpret_cast<const float4*>(S.W3t + k * kCMax);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) y[q] = fmaf(S.W3t[k * kCMax + tp + 4 * q], h, y[q]);
+        for (int q = 0; q < kCMax / 4; ++q) {
+          const float4 wq = w[q];
+          y[4 * q + 0] = fmaf(wq.x, h, y[4 * q + 0]);
+          y[4 * q + 1] = fmaf(wq.y, h, y[4 * q + 1]);
+          y[4 * q + 2] = fmaf(wq.z, h, y[4 * q + 2]);
+          y[4 * q + 3] = fmaf(wq.w, h, y[4 * q + 3]);
+        }
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = tp + 4 * q;
+      for (int c = 0; c < kCMax; ++c) {
         if (c >= C) continue;
         float d = 0.f;
         if (MODE == kModeFwd) {
-          if (valid) a.y[sid * C + c] = y[q];
+          if (valid) a.y[sid * C + c] = y[c];
         } else if (MODE == kModeBwd) {
           d = valid ? __ldg(a.dy + sid * C + c) : 0.f;
         } else {
-          const float r = y[q] - S.DY[c * kLd + ts];
+          const float r = y[c] - S.DY[c * kLd + t];
           if (valid) {
             neumaier(loss_s, loss_e, a.loss_l1 ? fabsf(r) : r * r);
             d = a.loss_l1 ? (r > 0.f ? a.scale : (r < 0.f ? -a.scale : 0.f)) : 2.f * r * a.scale;
           }
         }
-        if (MODE != kModeFwd) S.DY[c * kLd + ts] = d;
+        if (MODE != kModeFwd) S.DY[c * kLd + t] = d;
       }
     }
     if (MODE == kModeFwd) {
@@ -243,134 +324,158 @@ __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
       continue;
     }
     __syncthreads();
-    // ---- D2 = (W3^T dy) * [h2 > 0]
+    // ---- dW3 += DY H2^T, db3; D2 = (W3^T dy) * [h2 > 0] (into registers, then over H2)
     {
-      float acc[4][4] = {};
-#pragma unroll 4
-      for (int k = 0; k < kCMax; ++k) {
-        const float4 dv = *reinterpret_cast<const float4*>(S.DY + k * kLd + 4 * sg);
-        const float4 w = *reinterpret_cast<const float4*>(S.W3 + k * kH + 4 * ng);
-        const float av[4] = {dv.x, dv.y, dv.z, dv.w}, bv[4] = {w.x, w.y, w.z, w.w};
+      const int ra[1] = {w3c};
+      const int rb[4] = {w2i, w2i + 8, w2i + 16, w2i + 24};
+      float d3[1][4];
+      sample_dots<1, 4>(S.DY, ra, S.H2, rb, d3);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+      for (int q = 0; q < 4; ++q) neumaier(g3s[q], g3e[q], d3[0][q]);
+    }
+    float2 acc[4][8];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    gemm_8x8<kCMax>(S.DY, S.W3, sg, ng, acc);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float2 h[4];
+      load_samples(S.H2 + (8 * ng + j) * kLd, sg, h);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        acc[i][j] = make_float2(h[i].x > 0.f ? acc[i][j].x : 0.f, h[i].y > 0.f ? acc[i][j].y : 0.f);
+    }
+    if (t >= 2 * kH && t < 2 * kH + kCMax) {  // db3
+      float s = 0.f;
+      const float* row = S.DY + (t - 2 * kH) * kLd;
+      for (int i = 0; i < kTS; i += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(row + i);
+        s += (v.x + v.y) + (v.z + v.w);
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 h = *reinterpret_cast<const float4*>(S.H2 + (4 * ng + j) * kLd + 4 * sg);
-        acc[0][j] = h.x > 0.f ? acc[0][j] : 0.f;
-        acc[1][j] = h.y > 0.f ? acc[1][j] : 0.f;
-        acc[2][j] = h.z > 0.f ? acc[2][j] : 0.f;
-        acc[3][j] = h.w > 0.f ? acc[3][j] : 0.f;
-      }
-      store_4x4(S.D2, sg, ng, acc);
+      neumaier(gbs, gbe, s);
     }
     __syncthreads();
-    // ---- D1 = (W2^T d2) * [h1 > 0]
-    {
-      float acc[4][4] = {};
-      gemm_4x4<kH>(S.D2, S.W2, sg, ng, acc);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 h = *reinterpret_cast<const float4*>(S.H1 + (4 * ng + j) * kLd + 4 * sg);
-        acc[0][j] = h.x > 0.f ? acc[0][j] : 0.f;
-        acc[1][j] = h.y > 0.f ? acc[1][j] : 0.f;
-        acc[2][j] = h.z > 0.f ? acc[2][j] : 0.f;
-        acc[3][j] = h.w > 0.f ? acc[3][j] : 0.f;
-      }
-      store_4x4(S.D1, sg, ng, acc);
-    }
+    store_8x8(S.H2, sg, ng, acc);  // H2 now holds D2
     __syncthreads();
-    // ---- dx (level tp's 3 features) = W1^T d1, scattered into the latent gradient
+    // ---- dW2 += D2 H1^T, db2; D1 = (W2^T d2) * [h1 > 0] (into registers, then over H1)
     {
-      float dx[3] = {0.f, 0.f, 0.f};
-#pragma unroll 8
-      for (int k = 0; k < kH; ++k) {
-        const float d = S.D1[k * kLd + ts];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dx[c] = fmaf(S.W1[k * kIn + 3 * tp + c], d, dx[c]);
-      }
-      if (valid) {
-        const Taps T = clamp_taps(uv.x, uv.y, a.lw[tp], a.lh[tp], a.shift[tp]);
-        float* G = a.lgrad[tp];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          atomicAdd(G + 3 * T.i00 + c, T.w00 * dx[c]);
-          atomicAdd(G + 3 * T.i10 + c, T.w10 * dx[c]);
-          atomicAdd(G + 3 * T.i01 + c, T.w01 * dx[c]);
-          atomicAdd(G + 3 * T.i11 + c, T.w11 * dx[c]);
-        }
-      }
-    }
-    // ---- weight gradients of this tile (sums over its samples), into the running sums
-    {
-      // dW2[j][i] += sum_s d2[j][s] h1[i][s]: thread owns j = 4 (t>>4).., i = 4 (t&15)..
-      float acc[4][4] = {};
-      const int jg = t >> 4, ig = t & 15;
-#pragma unroll 4
-      for (int s = 0; s < kTS; ++s) {
-        float dv[4], hv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          dv[q] = S.D2[(4 * jg + q) * kLd + s];
-          hv[q] = S.H1[(4 * ig + q) * kLd + s];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(dv[i], hv[j], acc[i][j]);
-      }
+      const int ra[4] = {w2o, w2o + 4, w2o + 8, w2o + 12};
+      const int rb[4] = {w2i, w2i + 8, w2i + 16, w2i + 24};
+      float d2[4][4];
+      sample_dots<4, 4>(S.H2, ra, S.H1, rb, d2);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int g = kGW2 + (4 * jg + i) * kH + 4 * ig + j;
-          neumaier(S.gs[g], S.ge[g], acc[i][j]);
-        }
+        for (int j = 0; j < 4; ++j) neumaier(g2s[i][j], g2e[i][j], d2[i][j]);
     }
-    {
-      // dW1[j][i] += sum_s d1[j][s] x[i][s]: thread owns j = t>>2, i = 3 (t&3) .. +2
-      const int j = t >> 2, i0 = 3 * (t & 3);
-      float acc[3] = {0.f, 0.f, 0.f};
-#pragma unroll 4
-      for (int s = 0; s < kTS; ++s) {
-        const float d = S.D1[j * kLd + s];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) acc[q] = fmaf(d, S.X[(i0 + q) * kLd + s], acc[q]);
+    if (t >= kH && t < 2 * kH) {  // db2
+      float s = 0.f;
+      const float* row = S.H2 + (t - kH) * kLd;
+      for (int i = 0; i < kTS; i += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(row + i);
+        s += (v.x + v.y) + (v.z + v.w);
       }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) neumaier(S.gs[kGW1 + j * kIn + i0 + q], S.ge[kGW1 + j * kIn + i0 + q], acc[q]);
+      neumaier(gbs, gbe, s);
     }
-    {
-      // dW3[c][i] += sum_s dy[c][s] h2[i][s]: thread owns c = t>>4, i = 4 (t&15) .. +3
-      const int c = t >> 4, i0 = 4 * (t & 15);
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-      for (int s = 0; s < kTS; ++s) {
-        const float d = S.DY[c * kLd + s];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = fmaf(d, S.H2[(i0 + q) * kLd + s], acc[q]);
-      }
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) neumaier(S.gs[kGW3 + c * kH + i0 + q], S.ge[kGW3 + c * kH + i0 + q], acc[q]);
-    }
-    if (t < 2 * kH + kCMax) {
-      // biases: db1 (t < 64), db2 (64 <= t < 128), db3 (t >= 128)
-      const float* src = t < kH ? S.D1 + t * kLd : t < 2 * kH ? S.D2 + (t - kH) * kLd : S.DY + (t - 2 * kH) * kLd;
-      float acc = 0.f;
-#pragma unroll 8
-      for (int s = 0; s < kTS; ++s) acc += src[s];
-      neumaier(S.gs[kGB1 + t], S.ge[kGB1 + t], acc);
+      for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    gemm_8x8<kH>(S.H2, S.W2, sg, ng, acc);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float2 h[4];
+      load_samples(S.H1 + (8 * ng + j) * kLd, sg, h);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        acc[i][j] = make_float2(h[i].x > 0.f ? acc[i][j].x : 0.f, h[i].y > 0.f ? acc[i][j].y : 0.f);
     }
     __syncthreads();
+    store_8x8(S.H1, sg, ng, acc);  // H1 now holds D1
+    __syncthreads();
+    // ---- dW1 += D1 X^T, db1; dx = W1^T d1 (thread = sample) scattered into the latent gradients
+    {
+      const int ra[1] = {w1o};
+      const int rb[3] = {w1i, w1i + 4, w1i + 8};
+      float d1[1][3];
+      sample_dots<1, 3>(S.H1, ra, S.X, rb, d1);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) neumaier(g1s[q], g1e[q], d1[0][q]);
+    }
+    if (t < kH) {  // db1
+      float s = 0.f;
+      const float* row = S.H1 + t * kLd;
+      for (int i = 0; i < kTS; i += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(row + i);
+        s += (v.x + v.y) + (v.z + v.w);
+      }
+      neumaier(gbs, gbe, s);
+    }
+    {
+      float dx[kIn];
+#pragma unroll
+      for (int i = 0; i < kIn; ++i) dx[i] = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < kH; ++k) {
+        const float d = S.H1[k * kLd + t];
+        const float4* w = reinterpret_cast<const float4*>(S.W1 + k * kIn);
+#pragma unroll
+        for (int q = 0; q < kIn / 4; ++q) {
+          const float4 wq = w[q];
+          dx[4 * q + 0] = fmaf(wq.x, d, dx[4 * q + 0]);
+          dx[4 * q + 1] = fmaf(wq.y, d, dx[4 * q + 1]);
+          dx[4 * q + 2] = fmaf(wq.z, d, dx[4 * q + 2]);
+          dx[4 * q + 3] = fmaf(wq.w, d, dx[4 * q + 3]);
+        }
+      }
+      if (valid) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
+          float* G = a.lgrad[k];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float g = dx[3 * k + c];
+            atomicAdd(G + 3 * T.i00 + c, T.w00 * g);
+            atomicAdd(G + 3 * T.i10 + c, T.w10 * g);
+            atomicAdd(G + 3 * T.i01 + c, T.w01 * g);
+            atomicAdd(G + 3 * T.i11 + c, T.w11 * g);
+          }
+        }
+      }
+    }
+    __syncthreads();  // X, H1 (D1), H2 (D2), DY are rewritten by the next tile
   }
   if (MODE == kModeFwd) return;
   // ---- per-CTA partials: gradient sums and the loss
   float* part = a.part + (size_t)blockIdx.x * kPart;
-  for (int e = t; e < kGN; e += kTT) {
-    part[2 * e] = S.gs[e];
-    part[2 * e + 1] = S.ge[e];
+  {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int g = kGW2 + (w2o + 4 * i) * kH + w2i + 8 * j;
+        part[2 * g] = g2s[i][j];
+        part[2 * g + 1] = g2e[i][j];
+      }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int g = kGW1 + w1o * kIn + w1i + 4 * q;
+      part[2 * g] = g1s[q];
+      part[2 * g + 1] = g1e[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int g = kGW3 + w3c * kH + w2i + 8 * q;
+      part[2 * g] = g3s[q];
+      part[2 * g + 1] = g3e[q];
+    }
+    if (t < 2 * kH + kCMax) {  // b1 [64], b2 [64], b3 [16] are contiguous slots
+      part[2 * (kGB1 + t)] = gbs;
+      part[2 * (kGB1 + t) + 1] = gbe;
+    }
   }
   // loss: compensated block reduction (warp shuffles, then warps in fixed order)
   float ls = loss_s, le = loss_e;
