@@ -80,9 +80,15 @@ def test_decode_uv_list(nb, ctx, address):
     assert max_abs(y.cpu().numpy(), ref) <= TOL_FP32
 
 
-@pytest.mark.parametrize("dims", [[12, 16, 9], [12, 32, 9], [12, 64, 9], [12, 32, 32, 9], [12, 64, 64, 64, 9]])
-def test_decode_mlp_shapes(nb, ctx, dims):
-    wl = synth.small_decode_workload(256, dims, seed=90 + len(dims) + dims[1])
+@pytest.mark.parametrize("dims,layout", [([12, 16, 9], "B"), ([12, 32, 9], "B"), ([12, 64, 9], "B"),
+                                         ([12, 32, 32, 9], "B"), ([12, 64, 64, 64, 9], "B"), ([12, 16, 16, 9], "A"),
+                                         ([12, 32, 32, 32, 9], "A"), ([12, 16, 16, 16, 9], "B")])
+def test_decode_mlp_shapes(nb, ctx, dims, layout):
+    """Hidden widths 16 / 32 / 64 with 1-3 hidden layers on both latent layouts
+    (variant B: 1/4, 1/8, 1/16, 1/32 of the output side; variant A: 1/4, 1/4,
+    1/8, 1/8) -- the tiled kernel's instantiations."""
+    lv = None if layout == "B" else [64, 64, 32, 32]
+    wl = synth.small_decode_workload(256, dims, seed=90 + len(dims) + dims[1], level_sides=lv)
     mat = nb.Material.from_synth(wl.material)
     y = nb.decode(ctx, mat, grid=(256, 96))
     ctx.sync()
