@@ -46,7 +46,7 @@ extern "C" {
 typedef enum {
   NBTC_OK = 0,
   NBTC_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or descriptor   */
-  NBTC_ERR_UNSUPPORTED = 2, /* valid request this build has no kernel for    */
+  NBTC_ERR_UNSUPPORTED = 2, /* valid request the library has no kernel for */
   NBTC_ERR_CUDA = 3,        /* a CUDA runtime call failed                    */
   NBTC_ERR_TIMEOUT = 4,     /* a device-side bounded wait expired            */
   NBTC_ERR_BOUNDS = 5       /* a checked build caught an out-of-range index  */
