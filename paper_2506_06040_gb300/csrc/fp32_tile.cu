@@ -225,6 +225,214 @@ nbtc_status launch_tile(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* 
   return cuda_check(cudaGetLastError(), "launch k_decode_fp32_tile");
 }
 
+// ---- wide variant (hidden width 64, two hidden layers): one 512-thread CTA per
+// SM on 512-texel tiles, which leaves shared memory for a pair-swapped copy of
+// every weight row.  A thread's products then pair two texels with two neurons
+// in "diagonal" and "anti-diagonal" packed FMAs -- (a0, a1) x (w0, w1) and
+// (a0, a1) x (w1, w0) -- so no operand needs a broadcast register pair (no
+// register moves in the inner loops).
+constexpr int kTW = 512;   // texels per tile = threads per CTA
+constexpr int kD = 64;     // hidden width of the wide kernel
+
+template <int NHID>
+struct WideSmem {
+  float w1n[kIn * kD], w1s[kIn * kD];                                  // [k][n], pair-swapped copy
+  float whn[(NHID > 1 ? NHID - 1 : 1) * kD * kD], whs[(NHID > 1 ? NHID - 1 : 1) * kD * kD];
+  float won[kD * kOutMax], wos[kD * kOutMax];                          // output layer [k][c], swapped copy
+  float b[NHID * kD + kOutMax], bs[NHID * kD + kOutMax];               // biases and their swapped pairs
+  float x[kOutMax * kTW];                                              // features [k][texel]; output staging
+  float h[kD * kTW];                                                   // activations [n][texel]; column buffer
+};
+
+// Thread (sg, ng): texels 4 sg + {0..3} and 256 + 4 sg + {0..3} (texel pairs
+// i = 0..3), neurons 8 ng + {0..7} (neuron pairs p = 0..3).  dg[i][p] holds
+// (t_i0 x n_p0, t_i1 x n_p1), ad[i][p] holds (t_i0 x n_p1, t_i1 x n_p0).
+template <int K>
+__device__ __forceinline__ void gemm_diag(const float* __restrict__ A, const float* __restrict__ Bn,
+                                          const float* __restrict__ Bs, int sg, int ng, float2 (&dg)[4][4],
+                                          float2 (&ad)[4][4]) {
+#pragma unroll 2
+  for (int k = 0; k < K; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kTW + 4 * sg);
+    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kTW + kTW / 2 + 4 * sg);
+    const float4 n0 = *reinterpret_cast<const float4*>(Bn + k * kD + 8 * ng);
+    const float4 n1 = *reinterpret_cast<const float4*>(Bn + k * kD + 8 * ng + 4);
+    const float4 s0 = *reinterpret_cast<const float4*>(Bs + k * kD + 8 * ng);
+    const float4 s1 = *reinterpret_cast<const float4*>(Bs + k * kD + 8 * ng + 4);
+    const float2 av[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                          make_float2(a1.z, a1.w)};
+    const float2 wn[4] = {make_float2(n0.x, n0.y), make_float2(n0.z, n0.w), make_float2(n1.x, n1.y),
+                          make_float2(n1.z, n1.w)};
+    const float2 ws[4] = {make_float2(s0.x, s0.y), make_float2(s0.z, s0.w), make_float2(s1.x, s1.y),
+                          make_float2(s1.z, s1.w)};
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        dg[i][p] = __ffma2_rn(av[i], wn[p], dg[i][p]);
+        ad[i][p] = __ffma2_rn(av[i], ws[p], ad[i][p]);
+      }
+  }
+}
+
+__device__ __forceinline__ void init_diag(const float* __restrict__ b, const float* __restrict__ bs, int ng,
+                                          float2 (&dg)[4][4], float2 (&ad)[4][4]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float2 bn = *reinterpret_cast<const float2*>(b + 8 * ng + 2 * p);
+    const float2 bw = *reinterpret_cast<const float2*>(bs + 8 * ng + 2 * p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      dg[i][p] = bn;
+      ad[i][p] = bw;
+    }
+  }
+}
+
+// ReLU and store: neuron n_p0 of texels (t_i0, t_i1) = (dg.x, ad.y); n_p1 = (ad.x, dg.y).
+__device__ __forceinline__ void store_diag(float* __restrict__ H, int sg, int ng, const float2 (&dg)[4][4],
+                                           const float2 (&ad)[4][4]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    float* r0 = H + (8 * ng + 2 * p) * kTW;
+    float* r1 = r0 + kTW;
+    *reinterpret_cast<float4*>(r0 + 4 * sg) = make_float4(fmaxf(dg[0][p].x, 0.f), fmaxf(ad[0][p].y, 0.f),
+                                                          fmaxf(dg[1][p].x, 0.f), fmaxf(ad[1][p].y, 0.f));
+    *reinterpret_cast<float4*>(r0 + kTW / 2 + 4 * sg) = make_float4(fmaxf(dg[2][p].x, 0.f), fmaxf(ad[2][p].y, 0.f),
+                                                                     fmaxf(dg[3][p].x, 0.f), fmaxf(ad[3][p].y, 0.f));
+    *reinterpret_cast<float4*>(r1 + 4 * sg) = make_float4(fmaxf(ad[0][p].x, 0.f), fmaxf(dg[0][p].y, 0.f),
+                                                          fmaxf(ad[1][p].x, 0.f), fmaxf(dg[1][p].y, 0.f));
+    *reinterpret_cast<float4*>(r1 + kTW / 2 + 4 * sg) = make_float4(fmaxf(ad[2][p].x, 0.f), fmaxf(dg[2][p].y, 0.f),
+                                                                     fmaxf(ad[3][p].x, 0.f), fmaxf(dg[3][p].y, 0.f));
+  }
+}
+
+template <int NHID>
+__global__ void __launch_bounds__(kTW, 1) k_decode_fp32_wide(DecodeArgs a, const float* __restrict__ gW,
+                                                            const float* __restrict__ gB, int nout, int footprint) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WideSmem<NHID>& S = *reinterpret_cast<WideSmem<NHID>*>(smem_raw);
+  const int t = threadIdx.x;
+  // ---- weights: global [out][in] per layer -> shared [in][out] and the pair-swapped copy
+  {
+    auto put = [](float* n, float* sw, int idx, float v) {
+      n[idx] = v;
+      sw[idx ^ 1] = v;
+    };
+    int off = 0;
+    for (int e = t; e < kD * kIn; e += kTW) {
+      const int nn = e / kIn, k = e - nn * kIn;
+      put(S.w1n, S.w1s, k * kD + nn, gW[e]);
+    }
+    off += kD * kIn;
+    for (int l = 0; l < NHID - 1; ++l) {
+      for (int e = t; e < kD * kD; e += kTW) {
+        const int nn = e / kD, k = e - nn * kD;
+        put(S.whn + l * kD * kD, S.whs + l * kD * kD, k * kD + nn, gW[off + e]);
+      }
+      off += kD * kD;
+    }
+    for (int e = t; e < kD * kOutMax; e += kTW) {
+      const int c = e / kD, k = e - c * kD;
+      put(S.won, S.wos, k * kOutMax + c, c < nout ? gW[off + c * kD + k] : 0.f);
+    }
+    for (int e = t; e < NHID * kD + kOutMax; e += kTW) put(S.b, S.bs, e, e < NHID * kD + nout ? gB[e] : 0.f);
+  }
+  __syncthreads();
+  const int sg = t & 63, ng = t >> 6;  // 64 texel groups x 8 neuron groups (two warps per neuron group)
+  const int64_t tiles = (a.n + kTW - 1) / kTW;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t t0 = tile * kTW;
+    // ---- features -> x [k][texel]
+    float f[12];
+    if (footprint) {
+      footprint_features<kTW>(a, t0, t, reinterpret_cast<float4*>(S.h), 1, f);
+    } else {
+      const int64_t tex = t0 + t;
+      direct_features(a, tex < a.n ? tex : a.n - 1, f);
+    }
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) S.x[k * kTW + t] = f[k];
+    __syncthreads();
+    {
+      float2 dg[4][4], ad[4][4];
+      init_diag(S.b, S.bs, ng, dg, ad);
+      gemm_diag<kIn>(S.x, S.w1n, S.w1s, sg, ng, dg, ad);
+      store_diag(S.h, sg, ng, dg, ad);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int l = 0; l < NHID - 1; ++l) {
+      float2 dg[4][4], ad[4][4];
+      init_diag(S.b + (l + 1) * kD, S.bs + (l + 1) * kD, ng, dg, ad);
+      gemm_diag<kD>(S.h, S.whn + l * kD * kD, S.whs + l * kD * kD, sg, ng, dg, ad);
+      __syncthreads();
+      store_diag(S.h, sg, ng, dg, ad);
+      __syncthreads();
+    }
+    // ---- output layer: threads t < 256 take texel pairs (2t, 2t+1), 10 channels as 5 pairs
+    if (t < kTW / 2) {
+      float2 dg[5], ad[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        dg[c] = *reinterpret_cast<const float2*>(S.b + NHID * kD + 2 * c);
+        ad[c] = *reinterpret_cast<const float2*>(S.bs + NHID * kD + 2 * c);
+      }
+#pragma unroll 4
+      for (int k = 0; k < kD; ++k) {
+        const float2 hv = *reinterpret_cast<const float2*>(S.h + k * kTW + 2 * t);
+        const float2* wn = reinterpret_cast<const float2*>(S.won + k * kOutMax);
+        const float2* ws = reinterpret_cast<const float2*>(S.wos + k * kOutMax);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          dg[c] = __ffma2_rn(hv, wn[c], dg[c]);
+          ad[c] = __ffma2_rn(hv, ws[c], ad[c]);
+        }
+      }
+      // texel 2t: channels (2c, 2c+1) = (dg.x, ad.x); texel 2t+1: (ad.y, dg.y); staged in x
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        if (2 * c < nout) {
+          S.x[(2 * t) * nout + 2 * c] = dg[c].x;
+          S.x[(2 * t + 1) * nout + 2 * c] = ad[c].y;
+        }
+        if (2 * c + 1 < nout) {
+          S.x[(2 * t) * nout + 2 * c + 1] = ad[c].x;
+          S.x[(2 * t + 1) * nout + 2 * c + 1] = dg[c].y;
+        }
+      }
+    }
+    __syncthreads();
+    {
+      float* out = reinterpret_cast<float*>(a.out);
+      const int64_t valid = a.n - t0 < kTW ? a.n - t0 : kTW;
+      if (valid == kTW) {  // whole tile: 512 * nout contiguous floats, 16-byte aligned
+        const float4* src = reinterpret_cast<const float4*>(S.x);
+        float4* dst = reinterpret_cast<float4*>(out + t0 * nout);
+        for (int e = t; e < kTW * nout / 4; e += kTW) dst[e] = src[e];
+      } else {
+        for (int e = t; e < valid * nout; e += kTW) out[t0 * nout + e] = S.x[e];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int NHID>
+nbtc_status launch_wide(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, int footprint, cudaStream_t s) {
+  static_assert(NHID == 2, "the wide kernel is instantiated for two hidden layers");
+  const size_t smem = sizeof(WideSmem<NHID>);
+  auto kern = k_decode_fp32_wide<NHID>;
+  nbtc_status st =
+      cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
+  if (st) return st;
+  const int64_t tiles = (a.n + kTW - 1) / kTW;
+  int64_t grid = ctx->sm_count;
+  if (grid > tiles) grid = tiles;
+  kern<<<(int)grid, kTW, smem, s>>>(a, mlp->weights, mlp->biases, mlp->dims[mlp->num_layers], footprint);
+  return cuda_check(cudaGetLastError(), "launch k_decode_fp32_wide");
+}
+
 }  // namespace
 
 // Tiled FP32 decode for MLPs [12, D, .., D, C <= 16] with D in {16, 32, 64}
@@ -247,6 +455,13 @@ nbtc_status launch_decode_fp32_tile(nbtc_context* ctx, const DecodeArgs& a, cons
       case 2: return launch_tile<DD, 2>(ctx, a, mlp, fp, s);    \
       default: return launch_tile<DD, 3>(ctx, a, mlp, fp, s);   \
     }                                                           \
+  }
+  // hidden width 64 with 2 hidden layers and at most 10 outputs: the wide kernel
+  // (measured faster there; with one hidden layer the 256-texel tiles win)
+  if (D == 64 && L - 1 == 2 && mlp->dims[L] <= 10) {
+    bool fpw = a.uv == nullptr && (a.grid_w % kTW) == 0;
+    for (int k = 0; k < 4; ++k) fpw = fpw && (int64_t)(kTW - 1) * a.lv[k].w / a.grid_w + 3 <= kColCap;
+    if (fpw || !fp) return launch_wide<2>(ctx, a, mlp, fpw, s);
   }
   NBTC_TILE(16)
   NBTC_TILE(32)
