@@ -202,3 +202,54 @@ def test_full_size_batch(nb, ctx):
     info = plan.info()
     assert info["decode_tiles"] == sum(S * S // 128 for S in bw.sizes)
     plan.close()
+
+
+def test_full_size_anisotropic_and_lit_frames(nb, ctx):
+    """The benchmark's 3840x2160 frame with the anisotropic latent filter (cap 16)
+    and, separately, with the fused lighting pass: 6,000 sampled pixels each
+    against the oracle (the lit frame's shading from its own FP16 G-buffer)."""
+    bw = synth.batch_workload()
+    mats = [nb.Material.from_synth(m) for m in bw.materials]
+    rng = np.random.default_rng(8)
+    pix = rng.integers(0, bw.frame_w * bw.frame_h, 6000)
+    ids = bw.mat_id.reshape(-1)[pix]
+    # anisotropic
+    fa = _frame_tensors(bw)
+    fa["lod"] = torch.from_numpy(np.ascontiguousarray(bw.lod_bias)).cuda()
+    fa["duv"] = torch.from_numpy(np.ascontiguousarray(bw.duv)).cuda()
+    fa["max_aniso"] = 16
+    plan = nb.Batch(ctx, mats, None, fa, autotune=False)
+    plan.render()
+    ctx.sync()
+    got = fa["out"].view(-1, 9)[torch.from_numpy(pix).cuda()].float().cpu().numpy().astype(np.float64)
+    uv, duv, bias = bw.uv.reshape(-1, 2)[pix], bw.duv.reshape(-1, 4)[pix], bw.lod_bias.reshape(-1)[pix]
+    for m in np.unique(ids[ids >= 0]):
+        sel = ids == m
+        mat = bw.materials[m]
+        mips = [oracle.frame.level_mips_rgb(lv) for lv in mat.levels]
+        emu = oracle.frame.decode_pixels_aniso(mat, mips, uv[sel], duv[sel], bias[sel], 16, "fp16")
+        _check(got[sel], emu, mat, FEATURE_BOUND(int(sel.sum())), 2.0 ** -10, FRAC)
+    plan.close()
+    del fa
+    # lit
+    fl = _frame_tensors(bw)
+    shaded = torch.empty((bw.frame_h, bw.frame_w, 4), dtype=torch.float32, device="cuda")
+    light = {"light_dir": (0.3, 0.4, 1.0), "light_rgb": (3.0, 3.0, 3.0), "view_dir": (0.0, 0.0, 1.0),
+             "sky": (0.6, 0.7, 0.9), "ground": (0.15, 0.12, 0.1)}
+    fl["shaded"], fl["light"] = shaded, light
+    plan = nb.Batch(ctx, mats, None, fl, autotune=False)
+    plan.render()
+    ctx.sync()
+    keep = ids >= 0
+    y = fl["out"].view(-1, 9)[torch.from_numpy(pix[keep]).cuda()].float().cpu().numpy().astype(np.float64)
+    lit = shaded.view(-1, 4)[torch.from_numpy(pix[keep]).cuda()].cpu().numpy().astype(np.float64)
+    ref = oracle.shade.shade(y, light["light_dir"], light["light_rgb"], light["view_dir"], light["sky"], light["ground"])
+    _, n, rough, _, _ = oracle.shade.surface(y)
+    l = np.array(light["light_dir"]) / np.linalg.norm(light["light_dir"])
+    h = (l + np.array([0.0, 0.0, 1.0])) / np.linalg.norm(l + np.array([0.0, 0.0, 1.0]))
+    a2 = rough ** 4
+    x = np.maximum(n @ h, 0.0)
+    cond = 4.0 * x * x * (1.0 - a2) / (x * x * (a2 - 1.0) + 1.0)
+    bound = (256.0 + 16.0 * cond) * 2.0 ** -24 * np.abs(ref).max(axis=1) + 1e-6
+    assert np.all(np.abs(lit[:, :3] - ref).max(axis=1) <= bound)
+    plan.close()

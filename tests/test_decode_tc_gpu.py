@@ -194,6 +194,22 @@ def test_fp8_grid(nb, ctx, dims):
           f"emulator {np.round(np.abs(emu - ref).max(0), 4).tolist()}")
 
 
+def test_fp8_full_size_sampled(nb, ctx):
+    """The 4096^2, 12-64-64-64-9 FP8 decode as the benchmark runs it: 65,536
+    random texels and the border rows against the FP8 emulator."""
+    wl = synth.decode_workload(2)
+    mat, packed, scales = _fp8_setup(nb, ctx, wl, 4096, 4096)
+    y = nb.decode(ctx, mat, nb.FP8_E4M3, packed, grid=(4096, 4096))
+    ctx.sync()
+    rng = np.random.default_rng(9)
+    idx = np.concatenate([rng.integers(0, 4096 * 4096, 65536), np.arange(4096), 4096 * 4095 + np.arange(4096)])
+    got = y[torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
+    tex = [oracle.decode.level_rgb(lv) for lv in wl.material.levels]
+    emu = oracle.decode.decode_grid(wl.material, 4096, 4096, idx, precision="fp8", fp8=scales, tex=tex)
+    x = oracle.decode.features_at(wl.material, (idx % 4096 + 0.5) / 4096, (idx // 4096 + 0.5) / 4096, tex)
+    _check(got, emu, wl.material, x, 2.0 ** -3, 0.99)
+
+
 def test_fp8_calibration_matches_oracle(nb, ctx):
     wl = synth.decode_workload(2)
     _fp8_setup(nb, ctx, wl, 4096, 4096)

@@ -176,3 +176,37 @@ def test_invalid_arguments(nb, ctx):
     out = torch.empty(8 * 8 * 3, device="cuda")
     assert ctx.lib.nbtc_qat_decode(ctx.handle, ctypes.byref(q), ctypes.c_void_p(out.data_ptr()), None) == \
         _abi.ERR_INVALID_ARG
+
+
+def test_qat_full_size_step(nb, ctx):
+    """The benchmark's QAT configuration: levels 1024^2..128^2 of raw parameters
+    N(0, 1), target 2048^2 x 9, batch 2^20: loss, the straight-through gradients
+    and the MLP gradients against the oracle on the whole batch."""
+    wl = synth.train_workload(full=True)
+    rng = synth.Rng(1003, 9)
+    sides = wl.latent_sides
+    e0 = [rng.normal(s * s // 16 * 3, 1.0).reshape(s // 4, s // 4, 3).astype(np.float32) for s in sides]
+    e1 = [rng.normal(s * s // 16 * 3, 1.0).reshape(s // 4, s // 4, 3).astype(np.float32) for s in sides]
+    al = [rng.normal(s * s, 1.0).reshape(s, s).astype(np.float32) for s in sides]
+    from paper_2506_06040_gb300.train import QatModel
+    model = QatModel(e0, e1, al, wl.shifts, wl.mlp.weights, wl.mlp.biases)
+    uv = wl.uv(0)
+    T = [oracle.qat.decode(a, b, c) for a, b, c in zip(e0, e1, al)]
+    _, cache = oracle.train.forward(T, wl.shifts, wl.mlp.weights, wl.mlp.biases, uv)
+    keep = np.ones(len(uv), dtype=bool)
+    for z in cache["pre"][:-1]:
+        keep &= np.abs(z).min(axis=1) > 1e-5
+    uv = uv[keep]
+    assert len(uv) > 0.95 * wl.batch
+    st = oracle.qat.init_state(e0, e1, al, wl.mlp.weights, wl.mlp.biases)
+    ref = oracle.qat.train_step(st, wl.shifts, wl.target, uv)
+    loss = model.train_step(ctx, torch.from_numpy(uv).cuda(), torch.from_numpy(wl.target).cuda())
+    ctx.sync()
+    assert abs(float(loss.item()) - ref["loss"]) <= REL * ref["loss"]
+    for k in range(4):
+        _check_grad(model.g_e0[k].cpu().numpy(), ref["grad_e0"][k], f"e0_{k}")
+        _check_grad(model.g_e1[k].cpu().numpy(), ref["grad_e1"][k], f"e1_{k}")
+        _check_grad(model.g_alpha[k].cpu().numpy(), ref["grad_alpha"][k], f"alpha{k}")
+    gw = model.grad_w.cpu().numpy()
+    for l, ((w0, w1), _) in enumerate(model.layer_slices()):
+        _check_grad(gw[w0:w1], ref["grad_w"][l], f"W{l}")
