@@ -168,11 +168,20 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
  *    NBTC_FP16 / NBTC_FP8_E4M3: `packed_dev` from nbtc_pack_mlp() with the
  *    same precision, `out_dev` n x N FP16.  out_dev 16-byte aligned.
  * Shapes with a kernel: 4 latent levels, hidden width 16, 32 or 64 (all
- * hidden layers equal), 1-3 hidden layers, N <= 16 (tensor-core forms: hidden
- * width 64, N <= 16). */
+ * hidden layers equal), 1-3 hidden layers, N <= 16 (the tensor-core forms run
+ * widths 16 and 32 zero-padded to 64). */
 nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp,
                         int32_t precision, const void* packed_dev, const float* uv_dev,
                         int64_t n, int32_t grid_w, int32_t grid_h, void* out_dev, void* stream);
+
+/* Grid-mode decode of rows [row0, row0 + rows) of a grid_w x grid_h texel-centre
+ * grid (u = (i + 0.5) / grid_w, v = (row0 + j + 0.5) / grid_h) into out_dev,
+ * rows x grid_w x N (row-major): the same values nbtc_decode writes for those
+ * rows of the whole grid.  Lets a caller stream a large decode in row bands
+ * (e.g. overlapping each band's device-to-host copy with the next band's decode). */
+nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp, int32_t precision,
+                             const void* packed_dev, int32_t grid_w, int32_t grid_h, int32_t row0, int32_t rows,
+                             void* out_dev, void* stream);
 
 /* ------------------------------------------------------------------ training
  *

@@ -7,4 +7,5 @@ paths runs in the library's CUDA kernels.  Build the library with
 """
 from ._abi import (CLAMP, FP8_E4M3, FP16, FP32, LOSS_L1, LOSS_MSE, WRAP, NbtcError,  # noqa: F401
                    load)
-from .api import Batch, Context, Material, bc1_decode_level, decode, fp8_calibrate, pack_mlp  # noqa: F401
+from .api import (Batch, Context, Material, bc1_decode_level, decode, decode_to_host, fp8_calibrate,  # noqa: F401
+                  pack_mlp)

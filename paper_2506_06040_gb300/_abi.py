@@ -88,6 +88,8 @@ PROTOTYPES = {
                                    c_void_p, c_void_p]),
     "nbtc_decode": (c_int, [c_void_p, POINTER(Latents), POINTER(Mlp), c_int32, c_void_p, c_void_p, c_int64,
                             c_int32, c_int32, c_void_p, c_void_p]),
+    "nbtc_decode_rows": (c_int, [c_void_p, POINTER(Latents), POINTER(Mlp), c_int32, c_void_p, c_int32, c_int32,
+                                 c_int32, c_int32, c_void_p, c_void_p]),
     "nbtc_train_workspace_bytes": (c_int, [c_void_p, POINTER(TrainArgs), POINTER(c_size_t)]),
     "nbtc_train_step": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),
     "nbtc_forward_continuous": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p, c_void_p]),

@@ -138,9 +138,20 @@ def pack_mlp(ctx: Context, mat: Material, precision: int, act_absmax=None, strea
 
 
 def decode(ctx: Context, mat: Material, precision: int = _abi.FP32, packed=None, uv=None, grid=None,
-           out=None, stream=None) -> torch.Tensor:
+           out=None, stream=None, rows=None) -> torch.Tensor:
     """Decodes n texels: grid=(w, h) texel centres, or uv [n, 2] FP32 on the device.
+    rows=(row0, count) with a grid decodes only those rows of it.
     Returns [n, N] FP32 (FP32 form) or FP16 (tensor-core forms)."""
+    if rows is not None:
+        gw, gh = grid
+        r0, nr = rows
+        dt = torch.float32 if precision == _abi.FP32 else torch.float16
+        if out is None:
+            out = torch.empty((nr * gw, mat.n_out), dtype=dt, device=mat.device)
+        lat, m = mat.latents_struct(), mat.mlp_struct()
+        check(ctx.lib.nbtc_decode_rows(ctx.handle, byref(lat), byref(m), precision, _ptr(packed), gw, gh, r0, nr,
+                                       _ptr(out), _stream(stream)))
+        return out
     if uv is not None:
         assert uv.dtype == torch.float32 and uv.is_contiguous() and uv.dim() == 2 and uv.shape[1] == 2
         n, gw, gh = uv.shape[0], 0, 0
@@ -154,6 +165,35 @@ def decode(ctx: Context, mat: Material, precision: int = _abi.FP32, packed=None,
     check(ctx.lib.nbtc_decode(ctx.handle, byref(lat), byref(m), precision, _ptr(packed), _ptr(uv), n, gw, gh,
                               _ptr(out), _stream(stream)))
     return out
+
+
+def decode_to_host(ctx: Context, mat: Material, host_out: torch.Tensor, grid, precision: int = _abi.FP32,
+                   packed=None, bands: int = 8, stream=None, copy_stream=None) -> torch.Tensor:
+    """Grid decode streamed to a pinned host tensor host_out [w*h, N]: the grid is
+    decoded in `bands` row bands on `stream`, each band's device-to-host copy on
+    `copy_stream` overlapping the next band's decode (two device band buffers).
+    Returns host_out once the last copy is enqueued; synchronise copy_stream
+    before reading it."""
+    gw, gh = grid
+    stream = stream or torch.cuda.current_stream()
+    copy_stream = copy_stream or torch.cuda.Stream()
+    per = -(-gh // bands)
+    dt = torch.float32 if precision == _abi.FP32 else torch.float16
+    bufs = [torch.empty((per * gw, mat.n_out), dtype=dt, device=mat.device) for _ in range(2)]
+    done = [torch.cuda.Event(), torch.cuda.Event()]     # band decoded
+    freed = [torch.cuda.Event(), torch.cuda.Event()]    # band buffer copied out
+    for b, r0 in enumerate(range(0, gh, per)):
+        nr = min(per, gh - r0)
+        k = b & 1
+        if b >= 2:
+            stream.wait_event(freed[k])
+        decode(ctx, mat, precision, packed, grid=grid, rows=(r0, nr), out=bufs[k][:nr * gw], stream=stream)
+        done[k].record(stream)
+        copy_stream.wait_event(done[k])
+        with torch.cuda.stream(copy_stream):
+            host_out[r0 * gw:(r0 + nr) * gw].copy_(bufs[k][:nr * gw], non_blocking=True)
+        freed[k].record(copy_stream)
+    return host_out
 
 
 class Batch:

@@ -133,8 +133,9 @@ struct DecodeArgs {
   int32_t wrap;
   const float* uv;  // NULL = grid mode
   int64_t n;
-  int32_t grid_w, grid_h;
-  float inv_gw, inv_gh;
+  int32_t grid_w, grid_h;  // grid mode: texels per row, rows decoded by this call
+  int32_t row0;            // grid mode: first row (of the full grid) decoded by this call
+  float inv_gw, inv_gh;    // grid mode: 1 / width, 1 / height of the full grid
   void* out;
   int* status;
 };
@@ -151,7 +152,7 @@ __device__ __forceinline__ float2 texel_uv(const DecodeArgs& a, int64_t t) {
     j = t / a.grid_w;
     i = t - j * a.grid_w;
   }
-  return make_float2(((float)i + 0.5f) * a.inv_gw, ((float)j + 0.5f) * a.inv_gh);
+  return make_float2(((float)i + 0.5f) * a.inv_gw, ((float)(j + a.row0) + 0.5f) * a.inv_gh);
 }
 
 }  // namespace nbtc

@@ -242,6 +242,29 @@ nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_m
   }
 }
 
+nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp, int32_t precision,
+                             const void* packed_dev, int32_t grid_w, int32_t grid_h, int32_t row0, int32_t rows,
+                             void* out_dev, void* stream) {
+  nbtc_status st = enter(ctx);
+  if (st) return st;
+  if (grid_h <= 0 || row0 < 0 || rows < 0 || row0 > grid_h || rows > grid_h - row0)
+    return fail(NBTC_ERR_INVALID_ARG, "row range outside the grid");
+  DecodeArgs a;
+  if ((st = make_decode_args(ctx, lat, mlp, nullptr, (int64_t)grid_w * rows, grid_w, rows, out_dev, a))) return st;
+  if (rows == 0) return NBTC_OK;
+  a.row0 = row0;
+  a.inv_gh = 1.0f / (float)grid_h;
+  switch (precision) {
+    case NBTC_FP32:
+      return launch_decode_fp32(ctx, a, mlp, (cudaStream_t)stream);
+    case NBTC_FP16:
+    case NBTC_FP8_E4M3:
+      return launch_decode_tc(ctx, a, mlp, precision, packed_dev, (cudaStream_t)stream);
+    default:
+      return fail(NBTC_ERR_INVALID_ARG, "unknown precision");
+  }
+}
+
 nbtc_status nbtc_packed_mlp_bytes(const nbtc_mlp* mlp, int32_t precision, size_t* bytes) {
   nbtc_status st = check_mlp(mlp);
   if (st) return st;

@@ -91,7 +91,7 @@ __device__ __forceinline__ ColumnJob column_job(const DecodeArgs& a, const TileP
   J.k = (job >= P.pre[1]) + (job >= P.pre[2]) + (job >= P.pre[3]);
   J.rel = job - pick4(P.pre, J.k);
   const LevelView& L = a.lv[J.k];
-  const float v = ((float)P.j + 0.5f) * a.inv_gh;
+  const float v = ((float)(P.j + a.row0) + 0.5f) * a.inv_gh;
   const float ty = texel_coord(v, L.h, L.shift);
   const float fty = floorf(ty);
   J.fy = ty - fty;
@@ -240,7 +240,7 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
   if (C.job >= 0) {
     const int k = C.job & 3;
     const LevelView& L = a.lv[k];
-    const float ty = texel_coord(((float)j + 0.5f) * a.inv_gh, L.h, L.shift);
+    const float ty = texel_coord(((float)(j + a.row0) + 0.5f) * a.inv_gh, L.h, L.shift);
     const float fty = floorf(ty);
     const float fy = ty - fty;
     const int key = (int)fty;
@@ -260,7 +260,7 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
     sm100::sts128f(colbuf + 16u * (uint32_t)(k * kColCap + (C.job >> 2)), fmaf(fy, C.dc[0], C.c0[0]),
                    fmaf(fy, C.dc[1], C.c0[1]), fmaf(fy, C.dc[2], C.c0[2]), 0.f);
     // the next row's pair changes here too: start pulling its blocks into L1
-    const float tyn = texel_coord(((float)j + 1.5f) * a.inv_gh, L.h, L.shift);
+    const float tyn = texel_coord(((float)(j + a.row0) + 1.5f) * a.inv_gh, L.h, L.shift);
     const int keyn = (int)floorf(tyn);
     if (keyn != key && j + 1 < a.grid_h) {
       const int y0 = wrap_or_clamp(keyn, L.h, a.wrap), y1 = wrap_or_clamp(keyn + 1, L.h, a.wrap);

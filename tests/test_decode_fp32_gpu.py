@@ -146,3 +146,31 @@ def test_invalid_arguments(nb, ctx):
         nb.decode(ctx, mat, grid=(8, 8))
     assert e.value.code == _abi.ERR_INVALID_ARG
     ctx.sync()
+
+
+@pytest.mark.parametrize("dims", [[12, 64, 64, 9], [12, 32, 9], [12, 64, 64, 64, 9]])
+def test_row_bands_equal_the_whole_grid(nb, ctx, dims):
+    """nbtc_decode_rows: any band of rows is bit-identical to those rows of the
+    whole-grid decode (FP32 and, for width 64, FP16), and the banded host stream
+    reassembles the whole texture."""
+    wl = synth.small_decode_workload(1024, dims, seed=150 + len(dims))
+    mat = nb.Material.from_synth(wl.material)
+    gw, gh = 1024, 600
+    full = nb.decode(ctx, mat, grid=(gw, gh))
+    for r0, nr in ((0, 1), (7, 100), (100, 137), (599, 1), (512, 88)):
+        band = nb.decode(ctx, mat, grid=(gw, gh), rows=(r0, nr))
+        assert torch.equal(band, full[r0 * gw:(r0 + nr) * gw])
+    host = torch.empty((gw * gh, 9), dtype=torch.float32).pin_memory()
+    cs = torch.cuda.Stream()
+    nb.decode_to_host(ctx, mat, host, (gw, gh), bands=7, copy_stream=cs)
+    cs.synchronize()
+    assert torch.equal(host, full.cpu())
+    if dims[1] == 64:
+        packed = nb.pack_mlp(ctx, mat, nb.FP16)
+        f16 = nb.decode(ctx, mat, nb.FP16, packed, grid=(gw, gh))
+        for r0, nr in ((3, 50), (300, 300)):
+            band = nb.decode(ctx, mat, nb.FP16, packed, grid=(gw, gh), rows=(r0, nr))
+            assert torch.equal(band.view(torch.int16), f16[r0 * gw:(r0 + nr) * gw].view(torch.int16))
+    ctx.sync()
+    with pytest.raises(nb.NbtcError):
+        nb.decode(ctx, mat, grid=(gw, gh), rows=(590, 20))
