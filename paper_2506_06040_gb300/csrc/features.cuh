@@ -192,9 +192,10 @@ struct StripCache {
   int total;       // column jobs of the strip
   int job;         // own job: level | colbuf slot << 2 (-1: none)
   int jx;          // own job: latent column (wrapped or clamped)
-  int key;         // floor(ty) of the decoded pair (INT_MIN: none)
+  int key;         // floor(ty) of the decoded pair (INT_MIN + 1: none)
   uint32_t rel4;   // own texel: left tap's colbuf slot per level, 8 bits each
   float fx[4];     // own texel: horizontal weight per level
+  uint32_t t1;     // own job: RGB8 of texel (jx, y1) -- the next pair's (jx, y0) when the key steps by one
   float c0[3];     // own job: texel (jx, y0), RGB / 255
   float dc[3];     // own job: texel (jx, y1) minus texel (jx, y0), RGB / 255
 };
@@ -209,7 +210,7 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
   const float s = 1.0f / 255.0f;
   if (i0 != C.i0) {  // new strip: column plan, own job, own texel's taps
     C.i0 = i0;
-    C.key = INT_MIN;
+    C.key = INT_MIN + 1;  // no pair decoded (and key == C.key + 1 cannot hold)
     const float u0 = ((float)i0 + 0.5f) * a.inv_gw;
     const float u1 = ((float)(i0 + NT - 1) + 0.5f) * a.inv_gw;
     const float u = ((float)(i0 + tid) + 0.5f) * a.inv_gw;
@@ -245,11 +246,20 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
     const float fy = ty - fty;
     const int key = (int)fty;
     if (key != C.key) {
-      C.key = key;
-      const int y0 = wrap_or_clamp(key, L.h, a.wrap), y1 = wrap_or_clamp(key + 1, L.h, a.wrap);
+      // moving down one latent row, the new pair's upper texel is the old pair's
+      // lower one: decode only the new lower texel
       const uint64_t* col = L.blocks + (C.jx >> 2);
-      const uint32_t t0 = bc1_texel(__ldg(col + (size_t)(y0 >> 2) * L.wb), C.jx & 3, y0 & 3);
+      uint32_t t0;
+      if (key == C.key + 1) {
+        t0 = C.t1;
+      } else {
+        const int y0 = wrap_or_clamp(key, L.h, a.wrap);
+        t0 = bc1_texel(__ldg(col + (size_t)(y0 >> 2) * L.wb), C.jx & 3, y0 & 3);
+      }
+      const int y1 = wrap_or_clamp(key + 1, L.h, a.wrap);
       const uint32_t t1 = bc1_texel(__ldg(col + (size_t)(y1 >> 2) * L.wb), C.jx & 3, y1 & 3);
+      C.key = key;
+      C.t1 = t1;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float v0 = (float)((t0 >> (8 * c)) & 255u), v1 = (float)((t1 >> (8 * c)) & 255u);
@@ -263,10 +273,8 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
     const float tyn = texel_coord(((float)(j + a.row0) + 1.5f) * a.inv_gh, L.h, L.shift);
     const int keyn = (int)floorf(tyn);
     if (keyn != key && j + 1 < a.grid_h) {
-      const int y0 = wrap_or_clamp(keyn, L.h, a.wrap), y1 = wrap_or_clamp(keyn + 1, L.h, a.wrap);
-      const uint64_t* col = L.blocks + (C.jx >> 2);
-      sm100::prefetch_l1(col + (size_t)(y0 >> 2) * L.wb);
-      sm100::prefetch_l1(col + (size_t)(y1 >> 2) * L.wb);
+      const int y1 = wrap_or_clamp(keyn + 1, L.h, a.wrap);
+      sm100::prefetch_l1(L.blocks + (C.jx >> 2) + (size_t)(y1 >> 2) * L.wb);
     }
   }
   if (C.total > NT) {
