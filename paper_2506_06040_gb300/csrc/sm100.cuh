@@ -27,17 +27,6 @@ __device__ __forceinline__ void named_bar_arrive(int id, int nthreads) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Barrier over `nthreads` threads that also ORs a predicate across them.
-__device__ __forceinline__ bool named_bar_or(int id, int nthreads, bool pred) {
-  uint32_t out;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.b32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.b32 %0, 1, 0, q;\n}"
-      : "=r"(out)
-      : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
-      : "memory");
-  return out != 0;
-}
-
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
@@ -48,31 +37,6 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Non-blocking test of phase `parity`.
-__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // try_wait with a suspend-time hint: a thread whose phase is not complete
@@ -149,19 +113,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-#define NBTC_R16(i) "=r"(r[i + 0]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), "=r"(r[i + 4]), "=r"(r[i + 5]), \
-                    "=r"(r[i + 6]), "=r"(r[i + 7]), "=r"(r[i + 8]), "=r"(r[i + 9]), "=r"(r[i + 10]),             \
-                    "=r"(r[i + 11]), "=r"(r[i + 12]), "=r"(r[i + 13]), "=r"(r[i + 14]), "=r"(r[i + 15])
-
-// 32 lanes x 32 bits, 16 consecutive columns starting at taddr (one row per thread).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : NBTC_R16(0)
-      : "r"(taddr));
-}
-#undef NBTC_R16
-
 // 32 consecutive columns (two x16 loads) and the wait, in one statement: the
 // loaded registers come straight out of the asm, so no copies are needed to
 // tie them to a separate wait.
@@ -187,23 +138,6 @@ __device__ __forceinline__ void tmem_ld16_wait(uint32_t taddr, uint32_t* r) {
       : "memory");
 }
 
-#define NBTC_W16(i) "+r"(r[i + 0]), "+r"(r[i + 1]), "+r"(r[i + 2]), "+r"(r[i + 3]), "+r"(r[i + 4]), "+r"(r[i + 5]), \
-                    "+r"(r[i + 6]), "+r"(r[i + 7]), "+r"(r[i + 8]), "+r"(r[i + 9]), "+r"(r[i + 10]),             \
-                    "+r"(r[i + 11]), "+r"(r[i + 12]), "+r"(r[i + 13]), "+r"(r[i + 14]), "+r"(r[i + 15])
-
-// Waits for this thread's outstanding tcgen05.ld; the registers are tied to
-// the wait so no use of them is scheduled before it.
-__device__ __forceinline__ void tmem_wait_ld16(uint32_t* r) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" : NBTC_W16(0)::"memory");
-}
-__device__ __forceinline__ void tmem_wait_ld32(uint32_t* r) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" : NBTC_W16(0), NBTC_W16(16)::"memory");
-}
-__device__ __forceinline__ void tmem_wait_ld64(uint32_t* r) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" : NBTC_W16(0), NBTC_W16(16) ::"memory");
-  asm volatile("" : NBTC_W16(32), NBTC_W16(48)::"memory");
-}
-#undef NBTC_W16
 
 // ---------------------------------------------------------------- MMA
 
