@@ -274,10 +274,10 @@ def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
     backward into MLP and every latent texel, compensated reduction, Adam."""
     import torch
 
-    from paper_2506_06040_gb300.train import ContinuousModel
+    from paper_2506_06040_gb300.train import ContinuousModel, padded
     wl = synth.train_workload(full=True)
-    model = ContinuousModel.from_synth(wl)
-    tgt = torch.from_numpy(wl.target).cuda()
+    model = ContinuousModel.from_synth(wl)          # latents stored 4 floats per texel
+    tgt = padded(torch.from_numpy(wl.target).cuda())  # target resident as [2048][2048][12]
     uvs = [torch.from_numpy(wl.uv(i)).cuda() for i in range(4)]
     it = iter(range(1 << 30))
     t = _time_steps(lambda: model.train_step(ctx, uvs[next(it) % 4], tgt, stream=stream),
@@ -287,7 +287,7 @@ def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
     peak = _fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
     ctx.sync(stream)
     res = {"workload": wl.name, "steps_per_s": 1e3 / ms, "samples_per_s": wl.batch * 1e3 / ms, "ms_per_step": ms,
-           "kernels_per_step": 6,
+           "kernels_per_step": 6, "layout": "latents [h][w][4], target [h][w][12] (padding channels unused)",
            "roofline": {"bound": "alu", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "frac": flop / (ms * 1e-3) / 1e12 / peak,
                         "note": "whole step (forward, backward, reduction, Adam) against the FP32 FFMA peak"}}

@@ -189,10 +189,18 @@ nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const n
  * compressor's texture-unit replica, gradients through the MLP into every
  * latent texel, Adam with lr 1e-3 for the MLP and 1e-2 for the latents).  The
  * latents here are plain FP32 textures (before BC1 quantisation): level k is
- * latents[k] = [heights[k]][widths[k]][3], sampled bilinearly with clamp
- * addressing and the level's shift.  The MLP is [12, 64, 64, C] (C <= 16) in the
- * nbtc_mlp layout.  The target is [target_h][target_w][C] FP32, sampled
- * bilinearly (clamp, no shift) at the same uv.  Loss: mean over batch and
+ * latents[k] = [heights[k]][widths[k]][latent_stride], channels 0..2 used,
+ * sampled bilinearly with clamp addressing and the level's shift.  The MLP is
+ * [12, 64, 64, C] (C <= 16) in the nbtc_mlp layout.  The target is
+ * [target_h][target_w][target_stride] FP32, channels 0..C-1 used, sampled
+ * bilinearly (clamp, no shift) at the same uv.
+ *
+ * Layout: latent_stride 4 (a padding channel after RGB; latents and gradients
+ * 16-byte aligned) lets the kernels fetch a texel and add its gradient with one
+ * 16-byte access each instead of three 4-byte ones; the padding channel is read
+ * but never used, its gradient stays 0 and Adam leaves it unchanged.  A
+ * target_stride that is a multiple of 4 (16-byte aligned target) likewise reads
+ * the target 16 bytes at a time; its padding channels are never used.  Loss: mean over batch and
  * channels of (y - t)^2 (NBTC_LOSS_MSE) or |y - t| (NBTC_LOSS_L1).
  *
  * Gradient sums over the batch use compensated (Neumaier) FP32 summation;
@@ -222,6 +230,9 @@ typedef struct {
   int32_t loss;                             /* nbtc_loss */
   void* workspace;                          /* caller-owned scratch, 16-byte aligned */
   size_t workspace_bytes;                   /* >= nbtc_train_workspace_bytes() */
+  int32_t latent_stride;                    /* floats per texel of latents, latent_grads, latent_m,
+                                               latent_v: 3 or 4 (0 means 3) */
+  int32_t target_stride;                    /* floats per target texel, >= C (0 means C) */
 } nbtc_train_args;
 
 /* Scratch bytes the training calls need on this context's device. */

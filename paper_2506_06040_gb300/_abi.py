@@ -42,7 +42,7 @@ class TrainArgs(ctypes.Structure):
                 ("target_w", c_int32), ("target_h", c_int32), ("uv", c_void_p), ("batch", c_int64),
                 ("step", c_int32), ("lr_mlp", c_float), ("lr_latent", c_float), ("beta1", c_float),
                 ("beta2", c_float), ("eps", c_float), ("loss", c_int32), ("workspace", c_void_p),
-                ("workspace_bytes", c_size_t)]
+                ("workspace_bytes", c_size_t), ("latent_stride", c_int32), ("target_stride", c_int32)]
 
 
 class QatLevel(ctypes.Structure):

@@ -55,6 +55,8 @@ nbtc_status qat_decode(nbtc_context* ctx, const nbtc_qat_level* q, float* out, c
 nbtc_status qat_encode(nbtc_context* ctx, const nbtc_qat_level* q, uint64_t* blocks, cudaStream_t s);
 nbtc_status train_step_qat(nbtc_context* ctx, const nbtc_train_args* A, const nbtc_qat_level* levels, float* loss,
                            cudaStream_t s);
+// Floats per latent texel of a training call (3 or 4), 0 when the stride is invalid.
+int latent_stride(const nbtc_train_args* A);
 // One Adam update (the step's betas, eps and step number; learning rate lr) of n parameters.
 nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, float* p, const float* g, float* m,
                         float* v, int64_t n, cudaStream_t s);

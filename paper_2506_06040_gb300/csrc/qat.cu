@@ -62,24 +62,30 @@ __device__ __forceinline__ float3 endpoint_value(const float* e, const QatThresh
                      (float)qlevel(e[2], T.t5, 31) / 31.f);
 }
 
-// One thread per texel: T = (1 - a) E0 + a E1.
-__global__ void k_qat_decode(QatLevelDev L, float* __restrict__ out, QatThresholds T) {
+// One thread per texel: T = (1 - a) E0 + a E1, written with ls floats per texel
+// (3, or 4 with the padding channel set to 0).
+__global__ void k_qat_decode(QatLevelDev L, float* __restrict__ out, QatThresholds T, int ls) {
   const int64_t n = (int64_t)L.w * L.h;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int y = (int)(i / L.w), x = (int)(i - (int64_t)y * L.w);
     const int64_t b = (int64_t)(y >> 2) * (L.w >> 2) + (x >> 2);
     const float3 E0 = endpoint_value(L.e0 + 3 * b, T), E1 = endpoint_value(L.e1 + 3 * b, T);
     const float a = (float)qlevel(L.alpha[i], T.t2, 3) / 3.f;
-    out[3 * i + 0] = fmaf(a, E1.x - E0.x, E0.x);
-    out[3 * i + 1] = fmaf(a, E1.y - E0.y, E0.y);
-    out[3 * i + 2] = fmaf(a, E1.z - E0.z, E0.z);
+    const float t0 = fmaf(a, E1.x - E0.x, E0.x), t1 = fmaf(a, E1.y - E0.y, E0.y), t2 = fmaf(a, E1.z - E0.z, E0.z);
+    if (ls == 4) {
+      reinterpret_cast<float4*>(out)[i] = make_float4(t0, t1, t2, 0.f);
+    } else {
+      out[3 * i + 0] = t0;
+      out[3 * i + 1] = t1;
+      out[3 * i + 2] = t2;
+    }
   }
 }
 
 // One thread per block: straight-through gradients of its two endpoints and
-// sixteen blend factors from dL/dT.
+// sixteen blend factors from dL/dT (ls floats per texel).
 __global__ void k_qat_backward(QatLevelDev L, const float* __restrict__ dT, float* __restrict__ g_e0,
-                               float* __restrict__ g_e1, float* __restrict__ g_alpha, QatThresholds T) {
+                               float* __restrict__ g_e1, float* __restrict__ g_alpha, QatThresholds T, int ls) {
   const int wb = L.w >> 2;
   const int64_t nb = (int64_t)wb * (L.h >> 2);
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
@@ -91,7 +97,7 @@ __global__ void k_qat_backward(QatLevelDev L, const float* __restrict__ dT, floa
         const int64_t i = (int64_t)(4 * by + ty) * L.w + 4 * bx + tx;
         const float p = L.alpha[i];
         const float a = (float)qlevel(p, T.t2, 3) / 3.f;
-        const float d0 = dT[3 * i], d1 = dT[3 * i + 1], d2 = dT[3 * i + 2];
+        const float d0 = dT[ls * i], d1 = dT[ls * i + 1], d2 = dT[ls * i + 2];
         s0[0] = fmaf(d0, 1.f - a, s0[0]);
         s0[1] = fmaf(d1, 1.f - a, s0[1]);
         s0[2] = fmaf(d2, 1.f - a, s0[2]);
@@ -167,7 +173,7 @@ nbtc_status qat_decode(nbtc_context* ctx, const nbtc_qat_level* q, float* out, c
   nbtc_status st = check_qat_level(q, false);
   if (st) return st;
   if (!out) return fail(NBTC_ERR_INVALID_ARG, "out NULL");
-  k_qat_decode<<<grid_for(ctx, (int64_t)q->width * q->height), 256, 0, s>>>(level_dev(q), out, make_thresholds());
+  k_qat_decode<<<grid_for(ctx, (int64_t)q->width * q->height), 256, 0, s>>>(level_dev(q), out, make_thresholds(), 3);
   return cuda_check(cudaGetLastError(), "launch k_qat_decode");
 }
 
@@ -185,8 +191,12 @@ nbtc_status train_step_qat(nbtc_context* ctx, const nbtc_train_args* A, const nb
   if (!A || !levels) return fail(NBTC_ERR_INVALID_ARG, "args or levels NULL");
   if (A->num_levels != 4) return fail(NBTC_ERR_UNSUPPORTED, "training takes 4 latent levels");
   nbtc_status st;
+  const int ls = latent_stride(A);
+  if (!ls) return fail(NBTC_ERR_INVALID_ARG, "latent_stride must be 3 or 4 (0 means 3)");
   for (int k = 0; k < 4; ++k) {
     if ((st = check_qat_level(&levels[k], true))) return st;
+    if (ls == 4 && (!aligned(A->latents[k], 16) || !aligned(A->latent_grads[k], 16)))
+      return fail(NBTC_ERR_INVALID_ARG, "latent_stride 4 wants 16-byte aligned latents and gradients");
     if (levels[k].width != A->widths[k] || levels[k].height != A->heights[k])
       return fail(NBTC_ERR_INVALID_ARG, "QAT level size differs from the decoded latent size");
     if (!A->latents[k] || !A->latent_grads[k]) return fail(NBTC_ERR_INVALID_ARG, "latent or gradient NULL");
@@ -194,14 +204,14 @@ nbtc_status train_step_qat(nbtc_context* ctx, const nbtc_train_args* A, const nb
   const QatThresholds T = make_thresholds();
   for (int k = 0; k < 4; ++k) {
     k_qat_decode<<<grid_for(ctx, (int64_t)levels[k].width * levels[k].height), 256, 0, s>>>(
-        level_dev(&levels[k]), A->latents[k], T);
+        level_dev(&levels[k]), A->latents[k], T, ls);
     if ((st = cuda_check(cudaGetLastError(), "launch k_qat_decode"))) return st;
   }
   if ((st = train_step_impl(ctx, A, loss, s, 3, nullptr, nullptr, A->workspace, A->workspace_bytes))) return st;
   for (int k = 0; k < 4; ++k) {
     const nbtc_qat_level& q = levels[k];
     const int64_t nb = (int64_t)(q.width / 4) * (q.height / 4), nt = (int64_t)q.width * q.height;
-    k_qat_backward<<<grid_for(ctx, nb), 256, 0, s>>>(level_dev(&q), A->latent_grads[k], q.g_e0, q.g_e1, q.g_alpha, T);
+    k_qat_backward<<<grid_for(ctx, nb), 256, 0, s>>>(level_dev(&q), A->latent_grads[k], q.g_e0, q.g_e1, q.g_alpha, T, ls);
     if ((st = cuda_check(cudaGetLastError(), "launch k_qat_backward"))) return st;
     if ((st = launch_adam(ctx, A, A->lr_latent, q.e0, q.g_e0, q.m_e0, q.v_e0, 3 * nb, s))) return st;
     if ((st = launch_adam(ctx, A, A->lr_latent, q.e1, q.g_e1, q.m_e1, q.v_e1, 3 * nb, s))) return st;

@@ -42,6 +42,7 @@ struct TrainDev {
   const float* B;  // b1 [64], b2 [64], b3 [C]
   const float* target;
   int tw, th;
+  int ts;  // floats per target texel
   const float* uv;
   int64_t batch;
   int C;
@@ -176,7 +177,11 @@ __device__ __forceinline__ void sample_dots(const float* __restrict__ A, const i
 // running (Neumaier) sums of the weight-gradient entries it computes in
 // registers across tiles -- the same entries every tile -- and writes them to
 // the CTA's partial slots at the end.
-template <int MODE>
+// LV: latents and latent gradients hold 4 floats per texel (16-byte texel
+// loads and 16-byte gradient adds); TV: the target's texel stride is a multiple
+// of 4 floats (16-byte loads).  Both give the same arithmetic as the 3-float /
+// scalar forms, in the same order.
+template <int MODE, bool LV, bool TV>
 __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
@@ -233,20 +238,47 @@ __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
     for (int k = 0; k < 4; ++k) {
       const Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
       const float* L = a.lat[k];
+      if constexpr (LV) {
+        const float4* L4 = reinterpret_cast<const float4*>(L);
+        const float4 q00 = __ldg(L4 + T.i00), q10 = __ldg(L4 + T.i10), q01 = __ldg(L4 + T.i01),
+                     q11 = __ldg(L4 + T.i11);
+        const float f0 = T.w00 * q00.x + T.w10 * q10.x + T.w01 * q01.x + T.w11 * q11.x;
+        const float f1 = T.w00 * q00.y + T.w10 * q10.y + T.w01 * q01.y + T.w11 * q11.y;
+        const float f2 = T.w00 * q00.z + T.w10 * q10.z + T.w01 * q01.z + T.w11 * q11.z;
+        S.X[(3 * k + 0) * kLd + t] = valid ? f0 : 0.f;
+        S.X[(3 * k + 1) * kLd + t] = valid ? f1 : 0.f;
+        S.X[(3 * k + 2) * kLd + t] = valid ? f2 : 0.f;
+      } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float f = T.w00 * __ldg(L + 3 * T.i00 + c) + T.w10 * __ldg(L + 3 * T.i10 + c) +
-                        T.w01 * __ldg(L + 3 * T.i01 + c) + T.w11 * __ldg(L + 3 * T.i11 + c);
-        S.X[(3 * k + c) * kLd + t] = valid ? f : 0.f;
+        for (int c = 0; c < 3; ++c) {
+          const float f = T.w00 * __ldg(L + 3 * T.i00 + c) + T.w10 * __ldg(L + 3 * T.i10 + c) +
+                          T.w01 * __ldg(L + 3 * T.i01 + c) + T.w11 * __ldg(L + 3 * T.i11 + c);
+          S.X[(3 * k + c) * kLd + t] = valid ? f : 0.f;
+        }
       }
     }
     // ---- targets (train mode) -> DY rows (turned into dL/dy below)
     if (MODE == kModeTrain) {
       const Taps T = clamp_taps(uv.x, uv.y, a.tw, a.th, 0.f);
-      for (int c = 0; c < C; ++c) {
-        const float v = T.w00 * __ldg(a.target + (size_t)T.i00 * C + c) + T.w10 * __ldg(a.target + (size_t)T.i10 * C + c) +
-                        T.w01 * __ldg(a.target + (size_t)T.i01 * C + c) + T.w11 * __ldg(a.target + (size_t)T.i11 * C + c);
-        S.DY[c * kLd + t] = v;
+      const size_t ts = (size_t)a.ts;
+      if constexpr (TV) {
+        // rows >= C of DY stay 0 (the padding channels are never read into them)
+        for (int q = 0; 4 * q < C; ++q) {
+          const float4 v00 = __ldg(reinterpret_cast<const float4*>(a.target + T.i00 * ts) + q);
+          const float4 v10 = __ldg(reinterpret_cast<const float4*>(a.target + T.i10 * ts) + q);
+          const float4 v01 = __ldg(reinterpret_cast<const float4*>(a.target + T.i01 * ts) + q);
+          const float4 v11 = __ldg(reinterpret_cast<const float4*>(a.target + T.i11 * ts) + q);
+          S.DY[(4 * q) * kLd + t] = T.w00 * v00.x + T.w10 * v10.x + T.w01 * v01.x + T.w11 * v11.x;
+          if (4 * q + 1 < C) S.DY[(4 * q + 1) * kLd + t] = T.w00 * v00.y + T.w10 * v10.y + T.w01 * v01.y + T.w11 * v11.y;
+          if (4 * q + 2 < C) S.DY[(4 * q + 2) * kLd + t] = T.w00 * v00.z + T.w10 * v10.z + T.w01 * v01.z + T.w11 * v11.z;
+          if (4 * q + 3 < C) S.DY[(4 * q + 3) * kLd + t] = T.w00 * v00.w + T.w10 * v10.w + T.w01 * v01.w + T.w11 * v11.w;
+        }
+      } else {
+        for (int c = 0; c < C; ++c) {
+          const float v = T.w00 * __ldg(a.target + T.i00 * ts + c) + T.w10 * __ldg(a.target + T.i10 * ts + c) +
+                          T.w01 * __ldg(a.target + T.i01 * ts + c) + T.w11 * __ldg(a.target + T.i11 * ts + c);
+          S.DY[c * kLd + t] = v;
+        }
       }
     }
     __syncthreads();
@@ -435,13 +467,22 @@ __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
         for (int k = 0; k < 4; ++k) {
           const Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
           float* G = a.lgrad[k];
+          if constexpr (LV) {
+            float4* G4 = reinterpret_cast<float4*>(G);
+            const float g0 = dx[3 * k], g1 = dx[3 * k + 1], g2 = dx[3 * k + 2];
+            atomicAdd(G4 + T.i00, make_float4(T.w00 * g0, T.w00 * g1, T.w00 * g2, 0.f));
+            atomicAdd(G4 + T.i10, make_float4(T.w10 * g0, T.w10 * g1, T.w10 * g2, 0.f));
+            atomicAdd(G4 + T.i01, make_float4(T.w01 * g0, T.w01 * g1, T.w01 * g2, 0.f));
+            atomicAdd(G4 + T.i11, make_float4(T.w11 * g0, T.w11 * g1, T.w11 * g2, 0.f));
+          } else {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float g = dx[3 * k + c];
-            atomicAdd(G + 3 * T.i00 + c, T.w00 * g);
-            atomicAdd(G + 3 * T.i10 + c, T.w10 * g);
-            atomicAdd(G + 3 * T.i01 + c, T.w01 * g);
-            atomicAdd(G + 3 * T.i11 + c, T.w11 * g);
+            for (int c = 0; c < 3; ++c) {
+              const float g = dx[3 * k + c];
+              atomicAdd(G + 3 * T.i00 + c, T.w00 * g);
+              atomicAdd(G + 3 * T.i10 + c, T.w10 * g);
+              atomicAdd(G + 3 * T.i01 + c, T.w01 * g);
+              atomicAdd(G + 3 * T.i11 + c, T.w11 * g);
+            }
           }
         }
       }
@@ -558,6 +599,11 @@ __global__ void k_adam_latent(float* __restrict__ p, const float* __restrict__ g
 
 // ------------------------------------------------------------------ host
 
+int latent_stride(const nbtc_train_args* A) {
+  const int ls = A->latent_stride == 0 ? 3 : A->latent_stride;
+  return ls == 3 || ls == 4 ? ls : 0;
+}
+
 nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, float* p, const float* g, float* m,
                         float* v, int64_t n, cudaStream_t s) {
   AdamHyper h;
@@ -582,8 +628,12 @@ static nbtc_status check_train(const nbtc_train_args* A, bool need_target, bool 
       m.dims[3] > kCMax)
     return fail(NBTC_ERR_UNSUPPORTED, "training takes an MLP [12, 64, 64, C], C <= 16");
   if (!m.weights || !m.biases) return fail(NBTC_ERR_INVALID_ARG, "mlp weights/biases NULL");
+  const int ls = latent_stride(A);
+  if (!ls) return fail(NBTC_ERR_INVALID_ARG, "latent_stride must be 3 or 4 (0 means 3)");
   for (int k = 0; k < 4; ++k) {
     if (!A->latents[k] || !A->latent_grads[k]) return fail(NBTC_ERR_INVALID_ARG, "latent or gradient NULL");
+    if (ls == 4 && (!aligned(A->latents[k], 16) || !aligned(A->latent_grads[k], 16)))
+      return fail(NBTC_ERR_INVALID_ARG, "latent_stride 4 wants 16-byte aligned latents and gradients");
     if (A->widths[k] < 1 || A->heights[k] < 1 || A->widths[k] > (1 << 15) || A->heights[k] > (1 << 15))
       return fail(NBTC_ERR_INVALID_ARG, "latent size out of range");
     if (need_latent_adam && (!A->latent_m[k] || !A->latent_v[k]))
@@ -594,6 +644,8 @@ static nbtc_status check_train(const nbtc_train_args* A, bool need_target, bool 
   if (need_adam && A->step < 1) return fail(NBTC_ERR_INVALID_ARG, "step must be >= 1");
   if (need_target && (!A->target || A->target_w < 1 || A->target_h < 1))
     return fail(NBTC_ERR_INVALID_ARG, "target missing");
+  if (need_target && A->target_stride != 0 && A->target_stride < m.dims[3])
+    return fail(NBTC_ERR_INVALID_ARG, "target_stride < C");
   if (A->batch < 0) return fail(NBTC_ERR_INVALID_ARG, "batch < 0");
   if (A->batch > 0 && (!A->uv || !aligned(A->uv, 8))) return fail(NBTC_ERR_INVALID_ARG, "uv NULL or not 8-byte aligned");
   if (A->loss != NBTC_LOSS_MSE && A->loss != NBTC_LOSS_L1) return fail(NBTC_ERR_INVALID_ARG, "unknown loss");
@@ -624,6 +676,7 @@ static TrainDev make_dev(const nbtc_train_args* A, void* workspace) {
   d.target = A->target;
   d.tw = A->target_w;
   d.th = A->target_h;
+  d.ts = A->target_stride ? A->target_stride : A->mlp.dims[3];
   d.uv = A->uv;
   d.batch = A->batch;
   d.C = A->mlp.dims[3];
@@ -635,9 +688,9 @@ static TrainDev make_dev(const nbtc_train_args* A, void* workspace) {
   return d;
 }
 
-template <int MODE>
-static nbtc_status launch_train_kernel(nbtc_context* ctx, const TrainDev& d, int grid, cudaStream_t s) {
-  auto kern = k_train<MODE>;
+template <int MODE, bool LV, bool TV>
+static nbtc_status launch_k_train(const TrainDev& d, int grid, cudaStream_t s) {
+  auto kern = k_train<MODE, LV, TV>;
   nbtc_status st = cuda_check(
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)), "smem attr");
   if (st) return st;
@@ -645,11 +698,26 @@ static nbtc_status launch_train_kernel(nbtc_context* ctx, const TrainDev& d, int
   return cuda_check(cudaGetLastError(), "launch k_train");
 }
 
+// lv: 4-float latent texels; the 16-byte target path needs a target stride that
+// is a multiple of 4 floats and a 16-byte aligned target (train mode only).
+template <int MODE>
+static nbtc_status launch_train_kernel(const nbtc_train_args* A, const TrainDev& d, int grid, cudaStream_t s) {
+  const bool lv = latent_stride(A) == 4;
+  if constexpr (MODE == kModeTrain) {
+    const bool tv = d.ts % 4 == 0 && aligned(d.target, 16);
+    if (lv) return tv ? launch_k_train<MODE, true, true>(d, grid, s) : launch_k_train<MODE, true, false>(d, grid, s);
+    return tv ? launch_k_train<MODE, false, true>(d, grid, s) : launch_k_train<MODE, false, false>(d, grid, s);
+  } else {
+    return lv ? launch_k_train<MODE, true, false>(d, grid, s) : launch_k_train<MODE, false, false>(d, grid, s);
+  }
+}
+
 // Zeroes the latent gradients (this batch's gradient, not an accumulation).
 static nbtc_status zero_latent_grads(const nbtc_train_args* A, cudaStream_t s) {
   for (int k = 0; k < 4; ++k) {
     nbtc_status st = cuda_check(
-        cudaMemsetAsync(A->latent_grads[k], 0, sizeof(float) * 3 * (size_t)A->widths[k] * A->heights[k], s),
+        cudaMemsetAsync(A->latent_grads[k], 0, sizeof(float) * latent_stride(A) * (size_t)A->widths[k] * A->heights[k],
+                        s),
         "memset latent grads");
     if (st) return st;
   }
@@ -669,7 +737,7 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
     if (A->batch == 0) return NBTC_OK;
     if (!y) return fail(NBTC_ERR_INVALID_ARG, "y is NULL");
     d.y = y;
-    return launch_train_kernel<kModeFwd>(ctx, d, grid, s);
+    return launch_train_kernel<kModeFwd>(A, d, grid, s);
   }
   if (!workspace || !aligned(workspace, 16) || workspace_bytes < (size_t)grid * kPart * sizeof(float))
     return fail(NBTC_ERR_INVALID_ARG, "workspace NULL, misaligned or too small");
@@ -677,9 +745,9 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
   if (mode == kModeBwd) {
     if (!dy && A->batch > 0) return fail(NBTC_ERR_INVALID_ARG, "dy is NULL");
     d.dy = dy;
-    if ((st = launch_train_kernel<kModeBwd>(ctx, d, grid, s))) return st;
+    if ((st = launch_train_kernel<kModeBwd>(A, d, grid, s))) return st;
   } else {
-    if ((st = launch_train_kernel<kModeTrain>(ctx, d, grid, s))) return st;
+    if ((st = launch_train_kernel<kModeTrain>(A, d, grid, s))) return st;
   }
   const int C = A->mlp.dims[3];
   AdamHyper h;
@@ -700,7 +768,7 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
   if (latent_adam) {
     h.lr = A->lr_latent;
     for (int k = 0; k < 4; ++k) {
-      const int64_t n = 3 * (int64_t)A->widths[k] * A->heights[k];
+      const int64_t n = latent_stride(A) * (int64_t)A->widths[k] * A->heights[k];
       int g = (int)((n + 255) / 256);
       if (g > ctx->sm_count * 16) g = ctx->sm_count * 16;
       k_adam_latent<<<g, 256, 0, s>>>(A->latents[k], A->latent_grads[k], A->latent_m[k], A->latent_v[k], n, h);

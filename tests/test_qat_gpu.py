@@ -35,10 +35,10 @@ def _params(seed, sides, scale=2.0):
     return e0, e1, al
 
 
-def _model(e0, e1, al, mlp_seed=9, C=9):
+def _model(e0, e1, al, mlp_seed=9, C=9, latent_stride=4):
     from paper_2506_06040_gb300.train import QatModel
     mlp = synth.he_mlp(synth.Rng(mlp_seed, 2), [12, 64, 64, C])
-    return QatModel(e0, e1, al, synth.SHIFTS, mlp.weights, mlp.biases), mlp
+    return QatModel(e0, e1, al, synth.SHIFTS, mlp.weights, mlp.biases, latent_stride=latent_stride), mlp
 
 
 def _check_grad(got, ref, name):
@@ -114,9 +114,10 @@ def _qat_workload(seed=61):
     return sides, e0, e1, al, target, uv
 
 
-def test_qat_step_matches_oracle(nb, ctx):
+@pytest.mark.parametrize("latent_stride", [3, 4])
+def test_qat_step_matches_oracle(nb, ctx, latent_stride):
     sides, e0, e1, al, target, uv = _qat_workload()
-    model, mlp = _model(e0, e1, al)
+    model, mlp = _model(e0, e1, al, latent_stride=latent_stride)
     # kink-free batch on the decoded textures (see the continuous-latent tests)
     T = [oracle.qat.decode(a, b, c) for a, b, c in zip(e0, e1, al)]
     _, cache = oracle.train.forward(T, synth.SHIFTS, mlp.weights, mlp.biases, uv)
@@ -200,7 +201,8 @@ def test_qat_full_size_step(nb, ctx):
     assert len(uv) > 0.95 * wl.batch
     st = oracle.qat.init_state(e0, e1, al, wl.mlp.weights, wl.mlp.biases)
     ref = oracle.qat.train_step(st, wl.shifts, wl.target, uv)
-    loss = model.train_step(ctx, torch.from_numpy(uv).cuda(), torch.from_numpy(wl.target).cuda())
+    from paper_2506_06040_gb300.train import padded
+    loss = model.train_step(ctx, torch.from_numpy(uv).cuda(), padded(torch.from_numpy(wl.target).cuda()))
     ctx.sync()
     assert abs(float(loss.item()) - ref["loss"]) <= REL * ref["loss"]
     for k in range(4):

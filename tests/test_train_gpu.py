@@ -72,15 +72,21 @@ def _mid_workload(seed=77):
     return synth.TrainWorkload("train-mid", sides, synth.SHIFTS, lat, mlp, target, 20000 + 37, seed)
 
 
-@pytest.mark.parametrize("which", ["reduced", "mid"])
-@pytest.mark.parametrize("kind", ["mse", "l1"])
-def test_forward_loss_and_gradients(nb, ctx, which, kind):
-    from paper_2506_06040_gb300.train import ContinuousModel
+# (latent texel stride, target padded to a multiple of 4 channels): every pairing
+# of the 3- and 4-float latent forms with the scalar and 16-byte target reads
+@pytest.mark.parametrize("which,kind,layout", [
+    ("reduced", "mse", (4, True)), ("reduced", "l1", (3, False)),
+    ("mid", "mse", (4, True)), ("mid", "mse", (4, False)), ("mid", "l1", (3, False)), ("mid", "l1", (3, True))])
+def test_forward_loss_and_gradients(nb, ctx, which, kind, layout):
+    from paper_2506_06040_gb300.train import ContinuousModel, padded
     wl = synth.train_workload(full=False) if which == "reduced" else _mid_workload()
     uv = kink_free(wl, wl.uv(0))
-    model = ContinuousModel.from_synth(wl)
+    model = ContinuousModel.from_synth(wl, latent_stride=layout[0])
     uvd = torch.from_numpy(uv).cuda()
     tgt = torch.from_numpy(wl.target).cuda()
+    if layout[1]:
+        tgt = padded(tgt)
+        tgt[..., wl.target.shape[2]:] = float("nan")   # padding channels must never be read into the loss
     y = model.forward(ctx, uvd)
     ctx.sync()
     y_ref, loss_ref, dW, db, dlat = _oracle_grads(wl, uv, kind)
@@ -110,6 +116,10 @@ def test_adam_updates_three_steps(nb, ctx):
         assert np.abs(model.latents[k].cpu().numpy() - st["latents"][k]).max() <= 1e-2 * 1e-3
         m = model.latent_m[k].cpu().numpy()
         assert np.abs(m - st["m_latents"][k]).max() <= REL * np.abs(st["m_latents"][k]).max() + 1e-12
+        # the padding channel of the 4-float texels: zero gradient, untouched by Adam
+        for buf in (model.latents[k], model.latent_grads[k], model.latent_m[k], model.latent_v[k]):
+            assert buf._base is not None and buf._base.shape[2] == 4
+            assert float(buf._base[..., 3].abs().max()) == 0.0
 
 
 def test_full_size_step(nb, ctx):
@@ -120,20 +130,25 @@ def test_full_size_step(nb, ctx):
     wl = synth.train_workload(full=True)
     uv = kink_free(wl, wl.uv(0))
     assert len(uv) > 0.95 * wl.batch
-    model = ContinuousModel.from_synth(wl)
-    loss = model.train_step(ctx, torch.from_numpy(uv).cuda(), torch.from_numpy(wl.target).cuda())
+    from paper_2506_06040_gb300.train import padded
+    model = ContinuousModel.from_synth(wl)   # the benchmark's layouts: 4-float latents, padded target
+    loss = model.train_step(ctx, torch.from_numpy(uv).cuda(), padded(torch.from_numpy(wl.target).cuda()))
     ctx.sync()
     _, loss_ref, dW, db, dlat = _oracle_grads(wl, uv)
     assert abs(float(loss.item()) - loss_ref) <= REL * abs(loss_ref)
     _check_all_grads(model, dW, db, dlat)
 
 
-def test_autograd_function(nb, ctx):
+@pytest.mark.parametrize("lat_channels", [3, 4])
+def test_autograd_function(nb, ctx, lat_channels):
+    """Leaf latents [h, w, 3] (read 3 floats per texel) or [h, w, 4] with a padding
+    channel (16-byte texels; its gradient is 0)."""
     from paper_2506_06040_gb300.train import ContinuousModel, NbtcDecodeFn
     wl = synth.train_workload(full=False)
     uv = kink_free(wl, wl.uv(1))
     model = ContinuousModel.from_synth(wl)
-    lats = [l.clone().requires_grad_(True) for l in model.latents]
+    lats = [torch.nn.functional.pad(l, (0, lat_channels - 3)).contiguous().requires_grad_(True)
+            for l in model.latents]
     w = model.weights.clone().requires_grad_(True)
     b = model.biases.clone().requires_grad_(True)
     uvd = torch.from_numpy(uv).cuda()
@@ -148,7 +163,10 @@ def test_autograd_function(nb, ctx):
         _check_grad(gw[w0:w1], dW[l], f"W{l}")
         _check_grad(gb[b0:b1], db[l], f"b{l}")
     for k in range(4):
-        _check_grad(lats[k].grad.cpu().numpy(), dlat[k], f"latent{k}")
+        assert lats[k].grad.shape == lats[k].shape
+        _check_grad(lats[k].grad[..., :3].cpu().numpy(), dlat[k], f"latent{k}")
+        if lat_channels == 4:
+            assert float(lats[k].grad[..., 3].abs().max()) == 0.0
 
 
 def test_empty_batch_and_invalid(nb, ctx):
@@ -159,4 +177,30 @@ def test_empty_batch_and_invalid(nb, ctx):
     assert y.shape == (0, 9)
     with pytest.raises(nb.NbtcError):
         model.train_step(ctx, torch.from_numpy(wl.uv(0)).cuda(), None)  # no target
+    ctx.sync()
+
+
+def test_invalid_strides(nb, ctx):
+    import ctypes
+    from paper_2506_06040_gb300 import _abi
+    from paper_2506_06040_gb300.train import ContinuousModel
+    wl = synth.train_workload(full=False)
+    model = ContinuousModel.from_synth(wl)
+    uv = torch.from_numpy(wl.uv(0)).cuda()
+    tgt = torch.from_numpy(wl.target).cuda()
+    loss = torch.empty(1, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def run(edit):
+        a = model.args(uv, tgt)
+        model._workspace(ctx, a)
+        edit(a)
+        return ctx.lib.nbtc_train_step(ctx.handle, ctypes.byref(a), ctypes.c_void_p(loss.data_ptr()), s)
+
+    assert run(lambda a: setattr(a, "latent_stride", 5)) == _abi.ERR_INVALID_ARG
+    assert run(lambda a: setattr(a, "target_stride", 8)) == _abi.ERR_INVALID_ARG   # < C = 9
+    # 4-float texels must start on a 16-byte boundary
+    assert run(lambda a: a.latents.__setitem__(1, a.latents[1] + 4)) == _abi.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        model.train_step(ctx, uv, tgt[..., :8].contiguous())
     ctx.sync()
