@@ -167,6 +167,13 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
  *  - precision NBTC_FP32: `packed_dev` NULL, `out_dev` n x N FP32.
  *    NBTC_FP16 / NBTC_FP8_E4M3: `packed_dev` from nbtc_pack_mlp() with the
  *    same precision, `out_dev` n x N FP16.  out_dev 16-byte aligned.
+ *  - out_dev is device memory or, for NBTC_FP32 only, pinned host memory
+ *    (cudaHostAlloc / cudaHostRegister): the kernel then stores the texels
+ *    straight into host memory over the host link, with no staging buffer or
+ *    copy; completion is the stream's.  Pinned host output with NBTC_FP16 /
+ *    NBTC_FP8_E4M3 is NBTC_ERR_UNSUPPORTED (their kernels store with bulk
+ *    copies, kept to device memory); any other pointer (pageable host memory)
+ *    is NBTC_ERR_INVALID_ARG.
  * Shapes with a kernel: 4 latent levels, hidden width 16, 32 or 64 (all
  * hidden layers equal), 1-3 hidden layers, N <= 16 (the tensor-core forms run
  * widths 16 and 32 zero-padded to 64). */
@@ -178,7 +185,8 @@ nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_m
  * grid (u = (i + 0.5) / grid_w, v = (row0 + j + 0.5) / grid_h) into out_dev,
  * rows x grid_w x N (row-major): the same values nbtc_decode writes for those
  * rows of the whole grid.  Lets a caller stream a large decode in row bands
- * (e.g. overlapping each band's device-to-host copy with the next band's decode). */
+ * (e.g. overlapping each band's device-to-host copy with the next band's decode).
+ * out_dev follows nbtc_decode's rules. */
 nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp, int32_t precision,
                              const void* packed_dev, int32_t grid_w, int32_t grid_h, int32_t row0, int32_t rows,
                              void* out_dev, void* stream);

@@ -169,13 +169,18 @@ def decode(ctx: Context, mat: Material, precision: int = _abi.FP32, packed=None,
 
 def decode_to_host(ctx: Context, mat: Material, host_out: torch.Tensor, grid, precision: int = _abi.FP32,
                    packed=None, bands: int = 8, stream=None, copy_stream=None) -> torch.Tensor:
-    """Grid decode streamed to a pinned host tensor host_out [w*h, N]: the grid is
+    """Grid decode into a pinned host tensor host_out [w*h, N].  FP32: one decode
+    whose kernel stores the texels straight into host_out over the host link (no
+    device buffer, no copy; done when `stream` is).  FP16 / FP8: the grid is
     decoded in `bands` row bands on `stream`, each band's device-to-host copy on
-    `copy_stream` overlapping the next band's decode (two device band buffers).
-    Returns host_out once the last copy is enqueued; synchronise copy_stream
-    before reading it."""
+    `copy_stream` overlapping the next band's decode (two device band buffers);
+    done when copy_stream is.  Returns host_out once the work is enqueued."""
+    if host_out.device.type != "cpu" or not host_out.is_pinned():
+        raise ValueError("host_out must be a pinned host tensor")
     gw, gh = grid
     stream = stream or torch.cuda.current_stream()
+    if precision == _abi.FP32:
+        return decode(ctx, mat, precision, packed, grid=grid, out=host_out, stream=stream)
     copy_stream = copy_stream or torch.cuda.Stream()
     per = -(-gh // bands)
     dt = torch.float32 if precision == _abi.FP32 else torch.float16

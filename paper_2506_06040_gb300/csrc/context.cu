@@ -223,6 +223,27 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
   return launch_calibrate_fp32(ctx, a, mlp, step, act_absmax_dev, (cudaStream_t)stream);
 }
 
+// Where a decode may write: device (or managed) memory, or -- FP32 decodes,
+// whose kernels store with plain global stores -- pinned host memory, which the
+// kernel writes directly over the host link (its device address replaces out).
+static nbtc_status resolve_out(int32_t precision, DecodeArgs& a) {
+  cudaPointerAttributes pa;
+  const cudaError_t e = cudaPointerGetAttributes(&pa, a.out);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(NBTC_ERR_INVALID_ARG, "out is not a pointer CUDA knows");
+  }
+  if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) return NBTC_OK;
+  if (pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+    if (precision != NBTC_FP32)
+      return fail(NBTC_ERR_UNSUPPORTED, "pinned host output is for FP32 decodes; FP16 / FP8 decode into device memory");
+    a.out = pa.devicePointer;
+    if (!aligned(a.out, 16)) return fail(NBTC_ERR_INVALID_ARG, "out not 16-byte aligned");
+    return NBTC_OK;
+  }
+  return fail(NBTC_ERR_INVALID_ARG, "out is neither device memory nor pinned host memory");
+}
+
 nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp, int32_t precision,
                         const void* packed_dev, const float* uv_dev, int64_t n, int32_t grid_w,
                         int32_t grid_h, void* out_dev, void* stream) {
@@ -231,6 +252,7 @@ nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_m
   DecodeArgs a;
   if ((st = make_decode_args(ctx, lat, mlp, uv_dev, n, grid_w, grid_h, out_dev, a))) return st;
   if (n == 0) return NBTC_OK;
+  if ((st = resolve_out(precision, a))) return st;
   switch (precision) {
     case NBTC_FP32:
       return launch_decode_fp32(ctx, a, mlp, (cudaStream_t)stream);
@@ -252,6 +274,7 @@ nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const n
   DecodeArgs a;
   if ((st = make_decode_args(ctx, lat, mlp, nullptr, (int64_t)grid_w * rows, grid_w, rows, out_dev, a))) return st;
   if (rows == 0) return NBTC_OK;
+  if ((st = resolve_out(precision, a))) return st;
   a.row0 = row0;
   a.inv_gh = 1.0f / (float)grid_h;
   switch (precision) {

@@ -151,8 +151,9 @@ def test_invalid_arguments(nb, ctx):
 @pytest.mark.parametrize("dims", [[12, 64, 64, 9], [12, 32, 9], [12, 64, 64, 64, 9]])
 def test_row_bands_equal_the_whole_grid(nb, ctx, dims):
     """nbtc_decode_rows: any band of rows is bit-identical to those rows of the
-    whole-grid decode (FP32 and, for width 64, FP16), and the banded host stream
-    reassembles the whole texture."""
+    whole-grid decode (FP32 and, for width 64, FP16); FP32 decodes straight into
+    pinned host memory and the FP16 banded host stream reassemble the texture."""
+    from paper_2506_06040_gb300 import _abi
     wl = synth.small_decode_workload(1024, dims, seed=150 + len(dims))
     mat = nb.Material.from_synth(wl.material)
     gw, gh = 1024, 600
@@ -160,17 +161,36 @@ def test_row_bands_equal_the_whole_grid(nb, ctx, dims):
     for r0, nr in ((0, 1), (7, 100), (100, 137), (599, 1), (512, 88)):
         band = nb.decode(ctx, mat, grid=(gw, gh), rows=(r0, nr))
         assert torch.equal(band, full[r0 * gw:(r0 + nr) * gw])
-    host = torch.empty((gw * gh, 9), dtype=torch.float32).pin_memory()
-    cs = torch.cuda.Stream()
-    nb.decode_to_host(ctx, mat, host, (gw, gh), bands=7, copy_stream=cs)
-    cs.synchronize()
+    # FP32 straight into pinned host memory: the whole grid, and a band of rows
+    host = torch.full((gw * gh, 9), float("nan"), dtype=torch.float32).pin_memory()
+    nb.decode_to_host(ctx, mat, host, (gw, gh))
+    ctx.sync()
     assert torch.equal(host, full.cpu())
+    host.fill_(float("nan"))
+    nb.decode(ctx, mat, grid=(gw, gh), rows=(100, 137), out=host[100 * gw:237 * gw])
+    ctx.sync()
+    assert torch.equal(host[100 * gw:237 * gw], full[100 * gw:237 * gw].cpu())
+    assert torch.isnan(host[:100 * gw]).all() and torch.isnan(host[237 * gw:]).all()
     if dims[1] == 64:
         packed = nb.pack_mlp(ctx, mat, nb.FP16)
         f16 = nb.decode(ctx, mat, nb.FP16, packed, grid=(gw, gh))
         for r0, nr in ((3, 50), (300, 300)):
             band = nb.decode(ctx, mat, nb.FP16, packed, grid=(gw, gh), rows=(r0, nr))
             assert torch.equal(band.view(torch.int16), f16[r0 * gw:(r0 + nr) * gw].view(torch.int16))
+        # FP16 to the host: row bands on the device, each copied out while the next decodes
+        h16 = torch.empty((gw * gh, 9), dtype=torch.float16).pin_memory()
+        cs = torch.cuda.Stream()
+        nb.decode_to_host(ctx, mat, h16, (gw, gh), nb.FP16, packed, bands=7, copy_stream=cs)
+        cs.synchronize()
+        assert torch.equal(h16.view(torch.int16), f16.cpu().view(torch.int16))
+        # the tensor-core kernels do not write host memory
+        with pytest.raises(nb.NbtcError) as e:
+            nb.decode(ctx, mat, nb.FP16, packed, grid=(gw, gh), out=h16)
+        assert e.value.code == _abi.ERR_UNSUPPORTED
+    # pageable host memory is refused before any launch
+    with pytest.raises(nb.NbtcError) as e:
+        nb.decode(ctx, mat, grid=(gw, gh), out=torch.empty((gw * gh, 9), dtype=torch.float32))
+    assert e.value.code == _abi.ERR_INVALID_ARG
     ctx.sync()
     with pytest.raises(nb.NbtcError):
         nb.decode(ctx, mat, grid=(gw, gh), rows=(590, 20))
