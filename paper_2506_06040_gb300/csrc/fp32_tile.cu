@@ -244,17 +244,18 @@ struct WideSmem {
   float h[kD * kTW];                                                   // activations [n][texel]; column buffer
 };
 
-// Thread (sg, ng): texels 4 sg + {0..3} and 256 + 4 sg + {0..3} (texel pairs
-// i = 0..3), neurons 8 ng + {0..7} (neuron pairs p = 0..3).  dg[i][p] holds
-// (t_i0 x n_p0, t_i1 x n_p1), ad[i][p] holds (t_i0 x n_p1, t_i1 x n_p0).
-template <int K>
+// Thread (sg, ng) of a group tiling TW texels: texels 4 sg + {0..3} and
+// TW / 2 + 4 sg + {0..3} (texel pairs i = 0..3), neurons 8 ng + {0..7} (neuron
+// pairs p = 0..3).  dg[i][p] holds (t_i0 x n_p0, t_i1 x n_p1), ad[i][p] holds
+// (t_i0 x n_p1, t_i1 x n_p0).
+template <int K, int TW>
 __device__ __forceinline__ void gemm_diag(const float* __restrict__ A, const float* __restrict__ Bn,
                                           const float* __restrict__ Bs, int sg, int ng, float2 (&dg)[4][4],
                                           float2 (&ad)[4][4]) {
 #pragma unroll 2
   for (int k = 0; k < K; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(A + k * kTW + 4 * sg);
-    const float4 a1 = *reinterpret_cast<const float4*>(A + k * kTW + kTW / 2 + 4 * sg);
+    const float4 a0 = *reinterpret_cast<const float4*>(A + k * TW + 4 * sg);
+    const float4 a1 = *reinterpret_cast<const float4*>(A + k * TW + TW / 2 + 4 * sg);
     const float4 n0 = *reinterpret_cast<const float4*>(Bn + k * kD + 8 * ng);
     const float4 n1 = *reinterpret_cast<const float4*>(Bn + k * kD + 8 * ng + 4);
     const float4 s0 = *reinterpret_cast<const float4*>(Bs + k * kD + 8 * ng);
@@ -290,26 +291,33 @@ __device__ __forceinline__ void init_diag(const float* __restrict__ b, const flo
 }
 
 // ReLU and store: neuron n_p0 of texels (t_i0, t_i1) = (dg.x, ad.y); n_p1 = (ad.x, dg.y).
+template <int TW>
 __device__ __forceinline__ void store_diag(float* __restrict__ H, int sg, int ng, const float2 (&dg)[4][4],
                                            const float2 (&ad)[4][4]) {
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    float* r0 = H + (8 * ng + 2 * p) * kTW;
-    float* r1 = r0 + kTW;
+    float* r0 = H + (8 * ng + 2 * p) * TW;
+    float* r1 = r0 + TW;
     *reinterpret_cast<float4*>(r0 + 4 * sg) = make_float4(fmaxf(dg[0][p].x, 0.f), fmaxf(ad[0][p].y, 0.f),
                                                           fmaxf(dg[1][p].x, 0.f), fmaxf(ad[1][p].y, 0.f));
-    *reinterpret_cast<float4*>(r0 + kTW / 2 + 4 * sg) = make_float4(fmaxf(dg[2][p].x, 0.f), fmaxf(ad[2][p].y, 0.f),
-                                                                     fmaxf(dg[3][p].x, 0.f), fmaxf(ad[3][p].y, 0.f));
+    *reinterpret_cast<float4*>(r0 + TW / 2 + 4 * sg) = make_float4(fmaxf(dg[2][p].x, 0.f), fmaxf(ad[2][p].y, 0.f),
+                                                                    fmaxf(dg[3][p].x, 0.f), fmaxf(ad[3][p].y, 0.f));
     *reinterpret_cast<float4*>(r1 + 4 * sg) = make_float4(fmaxf(ad[0][p].x, 0.f), fmaxf(dg[0][p].y, 0.f),
                                                           fmaxf(ad[1][p].x, 0.f), fmaxf(dg[1][p].y, 0.f));
-    *reinterpret_cast<float4*>(r1 + kTW / 2 + 4 * sg) = make_float4(fmaxf(ad[2][p].x, 0.f), fmaxf(dg[2][p].y, 0.f),
-                                                                     fmaxf(ad[3][p].x, 0.f), fmaxf(dg[3][p].y, 0.f));
+    *reinterpret_cast<float4*>(r1 + TW / 2 + 4 * sg) = make_float4(fmaxf(ad[2][p].x, 0.f), fmaxf(dg[2][p].y, 0.f),
+                                                                    fmaxf(ad[3][p].x, 0.f), fmaxf(dg[3][p].y, 0.f));
   }
 }
 
-template <int NHID>
+// GR independent groups of kTW / GR threads, each on its own tiles of kTW / GR
+// texels with its own activation / feature buffers and its own named barrier
+// (id 1 + group): the groups drift out of phase, so one group's feature stage
+// (integer BC1 decode, loads, blends) overlaps the other's FMA-bound layers.
+// GR = 1 is one 512-texel group with block-wide barriers.
+template <int NHID, int GR>
 __global__ void __launch_bounds__(kTW, 1) k_decode_fp32_wide(DecodeArgs a, const float* __restrict__ gW,
                                                             const float* __restrict__ gB, int nout, int footprint) {
+  constexpr int TW = kTW / GR;  // texels per tile = threads per group
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WideSmem<NHID>& S = *reinterpret_cast<WideSmem<NHID>*>(smem_raw);
   const int t = threadIdx.x;
@@ -339,39 +347,51 @@ __global__ void __launch_bounds__(kTW, 1) k_decode_fp32_wide(DecodeArgs a, const
     for (int e = t; e < NHID * kD + kOutMax; e += kTW) put(S.b, S.bs, e, e < NHID * kD + nout ? gB[e] : 0.f);
   }
   __syncthreads();
-  const int sg = t & 63, ng = t >> 6;  // 64 texel groups x 8 neuron groups (two warps per neuron group)
-  const int64_t tiles = (a.n + kTW - 1) / kTW;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t t0 = tile * kTW;
+  const int g = GR == 1 ? 0 : t / TW, lt = GR == 1 ? t : t - g * TW;
+  const int bar = 1 + g;
+  auto group_sync = [&]() {
+    if constexpr (GR == 1) {
+      __syncthreads();
+    } else {
+      sm100::named_bar_sync(bar, TW);
+    }
+  };
+  float* X = S.x + g * (kOutMax * TW);  // features [k][texel]; output staging
+  float* Hb = S.h + g * (kD * TW);      // activations [n][texel]; column buffer
+  // TW / 8 texel groups x 8 neuron groups (a warp spans one neuron group)
+  const int sg = lt % (TW / 8), ng = lt / (TW / 8);
+  const int64_t tiles = (a.n + TW - 1) / TW;
+  for (int64_t tile = (int64_t)blockIdx.x * GR + g; tile < tiles; tile += (int64_t)gridDim.x * GR) {
+    const int64_t t0 = tile * TW;
     // ---- features -> x [k][texel]
     float f[12];
     if (footprint) {
-      footprint_features<kTW>(a, t0, t, reinterpret_cast<float4*>(S.h), 1, f);
+      footprint_features<TW>(a, t0, lt, reinterpret_cast<float4*>(Hb), bar, f);
     } else {
-      const int64_t tex = t0 + t;
+      const int64_t tex = t0 + lt;
       direct_features(a, tex < a.n ? tex : a.n - 1, f);
     }
 #pragma unroll
-    for (int k = 0; k < kIn; ++k) S.x[k * kTW + t] = f[k];
-    __syncthreads();
+    for (int k = 0; k < kIn; ++k) X[k * TW + lt] = f[k];
+    group_sync();
     {
       float2 dg[4][4], ad[4][4];
       init_diag(S.b, S.bs, ng, dg, ad);
-      gemm_diag<kIn>(S.x, S.w1n, S.w1s, sg, ng, dg, ad);
-      store_diag(S.h, sg, ng, dg, ad);
+      gemm_diag<kIn, TW>(X, S.w1n, S.w1s, sg, ng, dg, ad);
+      store_diag<TW>(Hb, sg, ng, dg, ad);
     }
-    __syncthreads();
+    group_sync();
 #pragma unroll 1
     for (int l = 0; l < NHID - 1; ++l) {
       float2 dg[4][4], ad[4][4];
       init_diag(S.b + (l + 1) * kD, S.bs + (l + 1) * kD, ng, dg, ad);
-      gemm_diag<kD>(S.h, S.whn + l * kD * kD, S.whs + l * kD * kD, sg, ng, dg, ad);
-      __syncthreads();
-      store_diag(S.h, sg, ng, dg, ad);
-      __syncthreads();
+      gemm_diag<kD, TW>(Hb, S.whn + l * kD * kD, S.whs + l * kD * kD, sg, ng, dg, ad);
+      group_sync();
+      store_diag<TW>(Hb, sg, ng, dg, ad);
+      group_sync();
     }
-    // ---- output layer: threads t < 256 take texel pairs (2t, 2t+1), 10 channels as 5 pairs
-    if (t < kTW / 2) {
+    // ---- output layer: threads lt < TW / 2 take texel pairs (2 lt, 2 lt + 1), 10 channels as 5 pairs
+    if (lt < TW / 2) {
       float2 dg[5], ad[5];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
@@ -380,7 +400,7 @@ __global__ void __launch_bounds__(kTW, 1) k_decode_fp32_wide(DecodeArgs a, const
       }
 #pragma unroll 4
       for (int k = 0; k < kD; ++k) {
-        const float2 hv = *reinterpret_cast<const float2*>(S.h + k * kTW + 2 * t);
+        const float2 hv = *reinterpret_cast<const float2*>(Hb + k * TW + 2 * lt);
         const float2* wn = reinterpret_cast<const float2*>(S.won + k * kOutMax);
         const float2* ws = reinterpret_cast<const float2*>(S.wos + k * kOutMax);
 #pragma unroll
@@ -389,46 +409,46 @@ __global__ void __launch_bounds__(kTW, 1) k_decode_fp32_wide(DecodeArgs a, const
           ad[c] = __ffma2_rn(hv, ws[c], ad[c]);
         }
       }
-      // texel 2t: channels (2c, 2c+1) = (dg.x, ad.x); texel 2t+1: (ad.y, dg.y); staged in x
+      // texel 2 lt: channels (2c, 2c+1) = (dg.x, ad.x); texel 2 lt + 1: (ad.y, dg.y); staged in x
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         if (2 * c < nout) {
-          S.x[(2 * t) * nout + 2 * c] = dg[c].x;
-          S.x[(2 * t + 1) * nout + 2 * c] = ad[c].y;
+          X[(2 * lt) * nout + 2 * c] = dg[c].x;
+          X[(2 * lt + 1) * nout + 2 * c] = ad[c].y;
         }
         if (2 * c + 1 < nout) {
-          S.x[(2 * t) * nout + 2 * c + 1] = ad[c].x;
-          S.x[(2 * t + 1) * nout + 2 * c + 1] = dg[c].y;
+          X[(2 * lt) * nout + 2 * c + 1] = ad[c].x;
+          X[(2 * lt + 1) * nout + 2 * c + 1] = dg[c].y;
         }
       }
     }
-    __syncthreads();
+    group_sync();
     {
       float* out = reinterpret_cast<float*>(a.out);
-      const int64_t valid = a.n - t0 < kTW ? a.n - t0 : kTW;
-      if (valid == kTW) {  // whole tile: 512 * nout contiguous floats, 16-byte aligned
-        const float4* src = reinterpret_cast<const float4*>(S.x);
+      const int64_t valid = a.n - t0 < TW ? a.n - t0 : TW;
+      if (valid == TW) {  // whole tile: TW * nout contiguous floats, 16-byte aligned
+        const float4* src = reinterpret_cast<const float4*>(X);
         float4* dst = reinterpret_cast<float4*>(out + t0 * nout);
-        for (int e = t; e < kTW * nout / 4; e += kTW) dst[e] = src[e];
+        for (int e = lt; e < TW * nout / 4; e += TW) dst[e] = src[e];
       } else {
-        for (int e = t; e < valid * nout; e += kTW) out[t0 * nout + e] = S.x[e];
+        for (int e = lt; e < valid * nout; e += TW) out[t0 * nout + e] = X[e];
       }
     }
-    __syncthreads();
+    group_sync();
   }
 }
 
-template <int NHID>
+template <int NHID, int GR>
 nbtc_status launch_wide(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp, int footprint, cudaStream_t s) {
   static_assert(NHID == 2, "the wide kernel is instantiated for two hidden layers");
   const size_t smem = sizeof(WideSmem<NHID>);
-  auto kern = k_decode_fp32_wide<NHID>;
+  auto kern = k_decode_fp32_wide<NHID, GR>;
   nbtc_status st =
       cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
   if (st) return st;
-  const int64_t tiles = (a.n + kTW - 1) / kTW;
+  const int64_t tiles = (a.n + kTW / GR - 1) / (kTW / GR);
   int64_t grid = ctx->sm_count;
-  if (grid > tiles) grid = tiles;
+  if (grid > (tiles + GR - 1) / GR) grid = (tiles + GR - 1) / GR;
   kern<<<(int)grid, kTW, smem, s>>>(a, mlp->weights, mlp->biases, mlp->dims[mlp->num_layers], footprint);
   return cuda_check(cudaGetLastError(), "launch k_decode_fp32_wide");
 }
@@ -459,9 +479,11 @@ nbtc_status launch_decode_fp32_tile(nbtc_context* ctx, const DecodeArgs& a, cons
   // hidden width 64 with 2 hidden layers and at most 10 outputs: the wide kernel
   // (measured faster there; with one hidden layer the 256-texel tiles win)
   if (D == 64 && L - 1 == 2 && mlp->dims[L] <= 10) {
-    bool fpw = a.uv == nullptr && (a.grid_w % kTW) == 0;
-    for (int k = 0; k < 4; ++k) fpw = fpw && (int64_t)(kTW - 1) * a.lv[k].w / a.grid_w + 3 <= kColCap;
-    if (fpw || !fp) return launch_wide<2>(ctx, a, mlp, fpw, s);
+    const int gr = ctx->fp32_groups == 1 ? 1 : 2;
+    const int tw = kTW / gr;
+    bool fpw = a.uv == nullptr && (a.grid_w % tw) == 0;
+    for (int k = 0; k < 4; ++k) fpw = fpw && (int64_t)(tw - 1) * a.lv[k].w / a.grid_w + 3 <= kColCap;
+    if (fpw || !fp) return gr == 1 ? launch_wide<2, 1>(ctx, a, mlp, fpw, s) : launch_wide<2, 2>(ctx, a, mlp, fpw, s);
   }
   NBTC_TILE(16)
   NBTC_TILE(32)

@@ -13,6 +13,7 @@ struct nbtc_context {
   int* status_dev = nullptr;       // device status word (first recorded fault)
   long long wait_budget = 0;       // spins per bounded device wait (0 = default)
   int tc_groups = 4;               // warpgroups per CTA of the tensor-core decode (3 or 4)
+  int fp32_groups = 2;             // independent thread groups per CTA of the FP32 wide decode (1 or 2)
 };
 
 namespace nbtc {
