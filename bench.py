@@ -443,7 +443,7 @@ def run_ours(args) -> dict | None:
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_tf, "traffic": _profiled_traffic("k_decode_fp32_wide_4096sq"),
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
-                     "kernel": "k_decode_fp32_wide<2>", "kernel_ms": kernel_ms},
+                     "kernel": "k_decode_fp32_wide<2, 2>", "kernel_ms": kernel_ms},
         "e2e": {"value": e2e, "unit": "Gtexel/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clk,
