@@ -204,3 +204,24 @@ def test_invalid_strides(nb, ctx):
     with pytest.raises(ValueError):
         model.train_step(ctx, uv, tgt[..., :8].contiguous())
     ctx.sync()
+
+
+def test_layouts_give_the_same_step(nb, ctx):
+    """4-float latent texels with a padded target run the 3-float form's arithmetic
+    term for term: the same loss and MLP gradients bit for bit; latent gradients
+    equal up to the order of the atomic adds."""
+    from paper_2506_06040_gb300.train import ContinuousModel, padded
+    wl = _mid_workload(seed=78)
+    uv = torch.from_numpy(wl.uv(0)).cuda()
+    tgt = torch.from_numpy(wl.target).cuda()
+    m3 = ContinuousModel.from_synth(wl, latent_stride=3)
+    m4 = ContinuousModel.from_synth(wl, latent_stride=4)
+    l3 = m3.train_step(ctx, uv, tgt)
+    l4 = m4.train_step(ctx, uv, padded(tgt))
+    ctx.sync()
+    assert torch.equal(l3, l4)
+    assert torch.equal(m3.grad_w, m4.grad_w) and torch.equal(m3.grad_b, m4.grad_b)
+    assert torch.equal(m3.weights, m4.weights)
+    for k in range(4):
+        g3, g4 = m3.latent_grads[k], m4.latent_grads[k]
+        assert (g3 - g4).abs().max().item() <= 1e-6 * g3.abs().max().item()
