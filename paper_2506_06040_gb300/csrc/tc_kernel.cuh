@@ -363,12 +363,14 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
               uint32_t w[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
+                // scale and bias as packed FMAs (two IEEE FP32 FMAs each)
                 const int j = 16 * c + 4 * e, jj = kPc * part + j;
-                w[e] = (uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j]), alp, b[jj]),
-                                                 fmaf(__uint_as_float(r[j + 1]), alp, b[jj + 1])) |
-                       ((uint32_t)cvt_relu_e4m3x2(fmaf(__uint_as_float(r[j + 2]), alp, b[jj + 2]),
-                                                  fmaf(__uint_as_float(r[j + 3]), alp, b[jj + 3]))
-                        << 16);
+                const float4 bb = *reinterpret_cast<const float4*>(b + jj);
+                const float2 v0 = __ffma2_rn(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
+                                             make_float2(alp, alp), make_float2(bb.x, bb.y));
+                const float2 v1 = __ffma2_rn(make_float2(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])),
+                                             make_float2(alp, alp), make_float2(bb.z, bb.w));
+                w[e] = (uint32_t)cvt_relu_e4m3x2(v0.x, v0.y) | ((uint32_t)cvt_relu_e4m3x2(v1.x, v1.y) << 16);
               }
               sts128(ah + off_sw64(gt, 16 * (part * (kPc / 16) + c)), w[0], w[1], w[2], w[3]);
             }
@@ -390,10 +392,18 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
         const float alp = alpha[NHID];
         const float* b = bias + NHID * kHid;
         uint16_t hv[kMaxOut];
+        if constexpr (FP8) {
 #pragma unroll
-        for (int k = 0; k < kMaxOut; ++k)
-          hv[k] = __half_as_ushort(FP8 ? __float2half_rn(fmaf(__uint_as_float(r[k]), alp, b[k]))
-                                       : __float2half_rn(__uint_as_float(r[k])));
+          for (int k = 0; k < kMaxOut; k += 2) {
+            const float2 v = __ffma2_rn(make_float2(__uint_as_float(r[k]), __uint_as_float(r[k + 1])),
+                                        make_float2(alp, alp), *reinterpret_cast<const float2*>(b + k));
+            hv[k] = __half_as_ushort(__float2half_rn(v.x));
+            hv[k + 1] = __half_as_ushort(__float2half_rn(v.y));
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < kMaxOut; ++k) hv[k] = __half_as_ushort(__float2half_rn(__uint_as_float(r[k])));
+        }
         if (MODE == kModeSingle || grid_chunk) {
           const int64_t t0 = tile_first_texel(D, hdiv, footprint, work.c.first + T);
           const int64_t tex = t0 + gt;
