@@ -104,7 +104,12 @@ typedef struct nbtc_context nbtc_context;
 /* Creates a context on CUDA device `device` (made current for the call).  The
  * context owns a 4-byte device status word and nothing else per device.
  * Returns NBTC_ERR_INVALID_ARG for a NULL `ctx`, NBTC_ERR_UNSUPPORTED when the
- * device is not compute capability 10.3, NBTC_ERR_CUDA when CUDA fails. */
+ * device is not compute capability 10.3, NBTC_ERR_CUDA when CUDA fails.
+ * Two environment variables, read here, select kernel shapes for measurement
+ * (results are identical either way): NBTC_TC_GROUPS=3 runs the single-material
+ * tensor-core decode with 3 warpgroups per CTA instead of 4, NBTC_FP32_GROUPS=1
+ * runs the FP32 wide decode as one 512-thread group per CTA instead of two
+ * independent 256-thread groups. */
 nbtc_status nbtc_create(int device, nbtc_context** ctx);
 
 /* Frees the context (synchronises the device first).  NULL is accepted. */

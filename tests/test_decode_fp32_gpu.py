@@ -69,6 +69,45 @@ def test_decode_ragged_grids(nb, ctx, gw, gh):
     assert max_abs(y.cpu().numpy(), ref) <= TOL_FP32
 
 
+@pytest.mark.parametrize("gw,gh", [(200, 136), (333, 3), (1, 1), (768, 5), (4096, 2), (1280, 9)])
+def test_decode_ragged_grids_wide(nb, ctx, gw, gh):
+    """The wide kernel (hidden width 64, two hidden layers): grids whose width is
+    not a multiple of its 256-texel tiles (per-texel features, ragged last tile),
+    widths that are (row-footprint features), and grids with fewer tiles than
+    thread groups."""
+    wl = synth.small_decode_workload(1024, [12, 64, 64, 9], seed=31)
+    mat = nb.Material.from_synth(wl.material)
+    y = nb.decode(ctx, mat, grid=(gw, gh))
+    ctx.sync()
+    ref = oracle.decode.decode_grid(wl.material, gw, gh)
+    assert max_abs(y.cpu().numpy(), ref) <= TOL_FP32
+
+
+def test_wide_kernel_group_counts_agree(nb):
+    """One 512-thread group per CTA (NBTC_FP32_GROUPS=1) and two 256-thread groups
+    compute every texel with the same arithmetic: bit-identical outputs."""
+    import os
+    wl = synth.small_decode_workload(1024, [12, 64, 64, 9], seed=32)
+    outs = []
+    for groups in ("1", "2"):
+        old = os.environ.get("NBTC_FP32_GROUPS")
+        os.environ["NBTC_FP32_GROUPS"] = groups
+        try:
+            c = nb.Context(0)
+        finally:
+            if old is None:
+                del os.environ["NBTC_FP32_GROUPS"]
+            else:
+                os.environ["NBTC_FP32_GROUPS"] = old
+        mat = nb.Material.from_synth(wl.material)
+        outs.append([nb.decode(c, mat, grid=g).cpu() for g in ((1024, 256), (1000, 37))])
+        outs[-1].append(nb.decode(c, mat, uv=torch.from_numpy(synth.random_uv(5, 3001)).cuda()).cpu())
+        c.sync()
+        c.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("address", ["clamp", "wrap"])
 def test_decode_uv_list(nb, ctx, address):
     wl = synth.small_decode_workload(128, [12, 64, 64, 9], seed=77, address=address)
@@ -191,6 +230,8 @@ def test_row_bands_equal_the_whole_grid(nb, ctx, dims):
     with pytest.raises(nb.NbtcError) as e:
         nb.decode(ctx, mat, grid=(gw, gh), out=torch.empty((gw * gh, 9), dtype=torch.float32))
     assert e.value.code == _abi.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        nb.decode_to_host(ctx, mat, torch.empty((gw * gh, 9), dtype=torch.float32), (gw, gh))
     ctx.sync()
     with pytest.raises(nb.NbtcError):
         nb.decode(ctx, mat, grid=(gw, gh), rows=(590, 20))
