@@ -51,6 +51,8 @@ struct TrainDev {
   const float* dy;  // backward mode
   float* y;         // forward mode
   float* part;      // [gridDim.x][kPart]
+  const float* xt;  // pre-gathered samples [batch][rs] (features, then target channels), or null
+  int rs;           // floats per pre-gathered sample
 };
 
 // Neumaier: (s, e) += x, exact sum ~ s + e
@@ -177,6 +179,85 @@ __device__ __forceinline__ void sample_dots(const float* __restrict__ A, const i
 // running (Neumaier) sums of the weight-gradient entries it computes in
 // registers across tiles -- the same entries every tile -- and writes them to
 // the CTA's partial slots at the end.
+// The 12 features of one sample (thread = sample): bilinear taps of the 4 latent
+// levels (3 or, LV, 4 floats per texel).
+template <bool LV>
+__device__ __forceinline__ void sample_features(const TrainDev& a, float u, float v, float (&f)[kIn]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const Taps T = clamp_taps(u, v, a.lw[k], a.lh[k], a.shift[k]);
+    const float* L = a.lat[k];
+    if constexpr (LV) {
+      const float4* L4 = reinterpret_cast<const float4*>(L);
+      const float4 q00 = __ldg(L4 + T.i00), q10 = __ldg(L4 + T.i10), q01 = __ldg(L4 + T.i01), q11 = __ldg(L4 + T.i11);
+      f[3 * k + 0] = T.w00 * q00.x + T.w10 * q10.x + T.w01 * q01.x + T.w11 * q11.x;
+      f[3 * k + 1] = T.w00 * q00.y + T.w10 * q10.y + T.w01 * q01.y + T.w11 * q11.y;
+      f[3 * k + 2] = T.w00 * q00.z + T.w10 * q10.z + T.w01 * q01.z + T.w11 * q11.z;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        f[3 * k + c] = T.w00 * __ldg(L + 3 * T.i00 + c) + T.w10 * __ldg(L + 3 * T.i10 + c) +
+                       T.w01 * __ldg(L + 3 * T.i01 + c) + T.w11 * __ldg(L + 3 * T.i11 + c);
+    }
+  }
+}
+
+// The target's C channels at one sample (bilinear, clamp, no shift), written to
+// out[c * stride]; TV: 16-byte reads of a texel stride that is a multiple of 4.
+template <bool TV>
+__device__ __forceinline__ void sample_target(const TrainDev& a, float u, float v, float* out, int stride) {
+  const Taps T = clamp_taps(u, v, a.tw, a.th, 0.f);
+  const size_t ts = (size_t)a.ts;
+  const int C = a.C;
+  if constexpr (TV) {
+    for (int q = 0; 4 * q < C; ++q) {
+      const float4 v00 = __ldg(reinterpret_cast<const float4*>(a.target + T.i00 * ts) + q);
+      const float4 v10 = __ldg(reinterpret_cast<const float4*>(a.target + T.i10 * ts) + q);
+      const float4 v01 = __ldg(reinterpret_cast<const float4*>(a.target + T.i01 * ts) + q);
+      const float4 v11 = __ldg(reinterpret_cast<const float4*>(a.target + T.i11 * ts) + q);
+      out[(4 * q) * stride] = T.w00 * v00.x + T.w10 * v10.x + T.w01 * v01.x + T.w11 * v11.x;
+      if (4 * q + 1 < C) out[(4 * q + 1) * stride] = T.w00 * v00.y + T.w10 * v10.y + T.w01 * v01.y + T.w11 * v11.y;
+      if (4 * q + 2 < C) out[(4 * q + 2) * stride] = T.w00 * v00.z + T.w10 * v10.z + T.w01 * v01.z + T.w11 * v11.z;
+      if (4 * q + 3 < C) out[(4 * q + 3) * stride] = T.w00 * v00.w + T.w10 * v10.w + T.w01 * v01.w + T.w11 * v11.w;
+    }
+  } else {
+    for (int c = 0; c < C; ++c)
+      out[c * stride] = T.w00 * __ldg(a.target + T.i00 * ts + c) + T.w10 * __ldg(a.target + T.i10 * ts + c) +
+                        T.w01 * __ldg(a.target + T.i01 * ts + c) + T.w11 * __ldg(a.target + T.i11 * ts + c);
+  }
+}
+
+// Floats per pre-gathered sample: 12 features (+ the target's C channels padded
+// to a multiple of 4 when the mode reads a target).
+__host__ __device__ inline int gathered_floats(int C, bool target) { return kIn + (target ? 4 * ((C + 3) / 4) : 0); }
+
+// k_gather: one thread per sample (many warps per SM, so the scattered latent
+// and target taps of many samples are in flight at once) writes the sample's
+// features and target channels as one contiguous record of a.rs floats, read
+// back by k_train with 16-byte coalesced loads.  Same arithmetic as k_train's
+// own gather.
+template <bool LV, bool TV>
+__global__ void __launch_bounds__(256) k_gather(TrainDev a, float* __restrict__ xt, int with_target) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.batch; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 uv = __ldg(reinterpret_cast<const float2*>(a.uv) + i);
+    float f[kIn];
+    sample_features<LV>(a, uv.x, uv.y, f);
+    float4* r = reinterpret_cast<float4*>(xt + i * a.rs);
+    r[0] = make_float4(f[0], f[1], f[2], f[3]);
+    r[1] = make_float4(f[4], f[5], f[6], f[7]);
+    r[2] = make_float4(f[8], f[9], f[10], f[11]);
+    if (with_target) {
+      float tv[kCMax];
+#pragma unroll
+      for (int c = 0; c < kCMax; ++c) tv[c] = 0.f;
+      sample_target<TV>(a, uv.x, uv.y, tv, 1);
+#pragma unroll
+      for (int q = 0; q < kCMax / 4; ++q)
+        if (4 * q < a.C) r[3 + q] = make_float4(tv[4 * q], tv[4 * q + 1], tv[4 * q + 2], tv[4 * q + 3]);
+    }
+  }
+}
+
 // LV: latents and latent gradients hold 4 floats per texel (16-byte texel
 // loads and 16-byte gradient adds); TV: the target's texel stride is a multiple
 // of 4 floats (16-byte loads).  Both give the same arithmetic as the 3-float /
@@ -233,53 +314,41 @@ __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
     const int64_t sid = tile * kTS + t;
     const bool valid = sid < a.batch;
     const float2 uv = valid ? __ldg(reinterpret_cast<const float2*>(a.uv) + sid) : make_float2(0.f, 0.f);
-    // ---- features (thread = sample): 4 levels x 3 channels
+    // ---- features and targets (thread = sample): pre-gathered records, or the taps here
+    if (a.xt) {
+      float4 r[3 + kCMax / 4];
+      const float4* rec = reinterpret_cast<const float4*>(a.xt + (valid ? sid : 0) * a.rs);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
-      const float* L = a.lat[k];
-      if constexpr (LV) {
-        const float4* L4 = reinterpret_cast<const float4*>(L);
-        const float4 q00 = __ldg(L4 + T.i00), q10 = __ldg(L4 + T.i10), q01 = __ldg(L4 + T.i01),
-                     q11 = __ldg(L4 + T.i11);
-        const float f0 = T.w00 * q00.x + T.w10 * q10.x + T.w01 * q01.x + T.w11 * q11.x;
-        const float f1 = T.w00 * q00.y + T.w10 * q10.y + T.w01 * q01.y + T.w11 * q11.y;
-        const float f2 = T.w00 * q00.z + T.w10 * q10.z + T.w01 * q01.z + T.w11 * q11.z;
-        S.X[(3 * k + 0) * kLd + t] = valid ? f0 : 0.f;
-        S.X[(3 * k + 1) * kLd + t] = valid ? f1 : 0.f;
-        S.X[(3 * k + 2) * kLd + t] = valid ? f2 : 0.f;
-      } else {
+      for (int q = 0; q < 3; ++q) r[q] = valid ? __ldg(rec + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (MODE == kModeTrain) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float f = T.w00 * __ldg(L + 3 * T.i00 + c) + T.w10 * __ldg(L + 3 * T.i10 + c) +
-                          T.w01 * __ldg(L + 3 * T.i01 + c) + T.w11 * __ldg(L + 3 * T.i11 + c);
-          S.X[(3 * k + c) * kLd + t] = valid ? f : 0.f;
+        for (int q = 0; q < kCMax / 4; ++q)
+          if (4 * q < C) r[3 + q] = valid ? __ldg(rec + 3 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        S.X[(4 * q + 0) * kLd + t] = r[q].x;
+        S.X[(4 * q + 1) * kLd + t] = r[q].y;
+        S.X[(4 * q + 2) * kLd + t] = r[q].z;
+        S.X[(4 * q + 3) * kLd + t] = r[q].w;
+      }
+      if (MODE == kModeTrain) {
+#pragma unroll
+        for (int q = 0; q < kCMax / 4; ++q) {
+          if (4 * q >= C) break;
+          S.DY[(4 * q) * kLd + t] = r[3 + q].x;
+          if (4 * q + 1 < C) S.DY[(4 * q + 1) * kLd + t] = r[3 + q].y;
+          if (4 * q + 2 < C) S.DY[(4 * q + 2) * kLd + t] = r[3 + q].z;
+          if (4 * q + 3 < C) S.DY[(4 * q + 3) * kLd + t] = r[3 + q].w;
         }
       }
-    }
-    // ---- targets (train mode) -> DY rows (turned into dL/dy below)
-    if (MODE == kModeTrain) {
-      const Taps T = clamp_taps(uv.x, uv.y, a.tw, a.th, 0.f);
-      const size_t ts = (size_t)a.ts;
-      if constexpr (TV) {
-        // rows >= C of DY stay 0 (the padding channels are never read into them)
-        for (int q = 0; 4 * q < C; ++q) {
-          const float4 v00 = __ldg(reinterpret_cast<const float4*>(a.target + T.i00 * ts) + q);
-          const float4 v10 = __ldg(reinterpret_cast<const float4*>(a.target + T.i10 * ts) + q);
-          const float4 v01 = __ldg(reinterpret_cast<const float4*>(a.target + T.i01 * ts) + q);
-          const float4 v11 = __ldg(reinterpret_cast<const float4*>(a.target + T.i11 * ts) + q);
-          S.DY[(4 * q) * kLd + t] = T.w00 * v00.x + T.w10 * v10.x + T.w01 * v01.x + T.w11 * v11.x;
-          if (4 * q + 1 < C) S.DY[(4 * q + 1) * kLd + t] = T.w00 * v00.y + T.w10 * v10.y + T.w01 * v01.y + T.w11 * v11.y;
-          if (4 * q + 2 < C) S.DY[(4 * q + 2) * kLd + t] = T.w00 * v00.z + T.w10 * v10.z + T.w01 * v01.z + T.w11 * v11.z;
-          if (4 * q + 3 < C) S.DY[(4 * q + 3) * kLd + t] = T.w00 * v00.w + T.w10 * v10.w + T.w01 * v01.w + T.w11 * v11.w;
-        }
-      } else {
-        for (int c = 0; c < C; ++c) {
-          const float v = T.w00 * __ldg(a.target + T.i00 * ts + c) + T.w10 * __ldg(a.target + T.i10 * ts + c) +
-                          T.w01 * __ldg(a.target + T.i01 * ts + c) + T.w11 * __ldg(a.target + T.i11 * ts + c);
-          S.DY[c * kLd + t] = v;
-        }
-      }
+    } else {
+      float f[kIn];
+      sample_features<LV>(a, uv.x, uv.y, f);
+#pragma unroll
+      for (int k = 0; k < kIn; ++k) S.X[k * kLd + t] = valid ? f[k] : 0.f;
+      // targets (train mode) -> DY rows (turned into dL/dy below); rows >= C stay 0
+      if (MODE == kModeTrain) sample_target<TV>(a, uv.x, uv.y, S.DY + t, kLd);
     }
     __syncthreads();
     // ---- H1 = ReLU(W1 x + b1), H2 = ReLU(W2 h1 + b2)
@@ -658,8 +727,15 @@ static int train_grid(nbtc_context* ctx, int64_t batch) {
   return g < 1 ? 1 : (int)g;
 }
 
+// Workspace: the per-CTA partial sums, then (from a 256-byte boundary) one
+// pre-gathered record per sample.  A workspace that only holds the partials is
+// accepted too; the step then gathers inside k_train.
+static size_t partials_bytes(int grid) { return ((size_t)grid * kPart * sizeof(float) + 255) & ~(size_t)255; }
+
 size_t train_workspace(nbtc_context* ctx, const nbtc_train_args* A) {
-  return (size_t)train_grid(ctx, A->batch) * kPart * sizeof(float);
+  const int C = A->mlp.num_layers == 3 ? A->mlp.dims[3] : kCMax;
+  return partials_bytes(train_grid(ctx, A->batch)) +
+         (size_t)(A->batch > 0 ? A->batch : 0) * gathered_floats(C, true) * sizeof(float);
 }
 
 static TrainDev make_dev(const nbtc_train_args* A, void* workspace) {
@@ -685,7 +761,35 @@ static TrainDev make_dev(const nbtc_train_args* A, void* workspace) {
   d.dy = nullptr;
   d.y = nullptr;
   d.part = static_cast<float*>(workspace);
+  d.xt = nullptr;
+  d.rs = 0;
   return d;
+}
+
+template <bool LV, bool TV>
+static nbtc_status launch_k_gather(nbtc_context* ctx, const TrainDev& d, float* xt, int with_target, cudaStream_t s) {
+  int64_t g = (d.batch + 255) / 256;
+  if (g > (int64_t)ctx->sm_count * 8) g = (int64_t)ctx->sm_count * 8;
+  k_gather<LV, TV><<<(int)g, 256, 0, s>>>(d, xt, with_target);
+  return cuda_check(cudaGetLastError(), "launch k_gather");
+}
+
+// Pre-gathers the batch's samples into the workspace when it has room for them.
+static nbtc_status pre_gather(nbtc_context* ctx, const nbtc_train_args* A, TrainDev& d, int grid, bool target,
+                              void* workspace, size_t workspace_bytes, cudaStream_t s) {
+  const int rs = gathered_floats(d.C, target);
+  const size_t off = partials_bytes(grid);
+  if (A->batch <= 0 || workspace_bytes < off + (size_t)A->batch * rs * sizeof(float)) return NBTC_OK;
+  float* xt = reinterpret_cast<float*>(static_cast<char*>(workspace) + off);
+  d.rs = rs;
+  const bool lv = latent_stride(A) == 4, tv = target && d.ts % 4 == 0 && aligned(d.target, 16);
+  nbtc_status st = lv ? (tv ? launch_k_gather<true, true>(ctx, d, xt, target, s)
+                            : launch_k_gather<true, false>(ctx, d, xt, target, s))
+                      : (tv ? launch_k_gather<false, true>(ctx, d, xt, target, s)
+                            : launch_k_gather<false, false>(ctx, d, xt, target, s));
+  if (st) return st;
+  d.xt = xt;
+  return NBTC_OK;
 }
 
 template <int MODE, bool LV, bool TV>
@@ -742,6 +846,7 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
   if (!workspace || !aligned(workspace, 16) || workspace_bytes < (size_t)grid * kPart * sizeof(float))
     return fail(NBTC_ERR_INVALID_ARG, "workspace NULL, misaligned or too small");
   if ((st = zero_latent_grads(A, s))) return st;
+  if ((st = pre_gather(ctx, A, d, grid, mode == kModeTrain, workspace, workspace_bytes, s))) return st;
   if (mode == kModeBwd) {
     if (!dy && A->batch > 0) return fail(NBTC_ERR_INVALID_ARG, "dy is NULL");
     d.dy = dy;

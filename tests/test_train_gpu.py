@@ -225,3 +225,33 @@ def test_layouts_give_the_same_step(nb, ctx):
     for k in range(4):
         g3, g4 = m3.latent_grads[k], m4.latent_grads[k]
         assert (g3 - g4).abs().max().item() <= 1e-6 * g3.abs().max().item()
+
+
+def test_pre_gathered_and_fused_gather_agree(nb, ctx):
+    """With a workspace that has room for the batch, the step gathers every
+    sample's features and target into the workspace first (k_gather); with one
+    that only holds the partial sums it gathers inside the training kernel.
+    Same arithmetic: the same loss and MLP gradients bit for bit."""
+    import ctypes
+    from paper_2506_06040_gb300.train import ContinuousModel, padded
+    wl = _mid_workload(seed=79)
+    uv = torch.from_numpy(wl.uv(0)).cuda()
+    tgt = padded(torch.from_numpy(wl.target).cuda())
+    losses, grads = [], []
+    for small in (False, True):
+        m = ContinuousModel.from_synth(wl)
+        a = m.args(uv, tgt)
+        m._workspace(ctx, a)
+        if small:   # room for the per-CTA partial sums only (2 x 6033 floats per CTA, one CTA per tile or SM)
+            grid = min(-(-int(uv.shape[0]) // 256), torch.cuda.get_device_properties(0).multi_processor_count)
+            a.workspace_bytes = grid * 2 * 6033 * 4
+        loss = torch.empty(1, device="cuda")
+        assert ctx.lib.nbtc_train_step(ctx.handle, ctypes.byref(a), ctypes.c_void_p(loss.data_ptr()),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+        ctx.sync()
+        losses.append(loss.clone())
+        grads.append((m.grad_w.clone(), m.grad_b.clone(), [g.clone() for g in m.latent_grads]))
+    assert torch.equal(losses[0], losses[1])
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
+    for g0, g1 in zip(grads[0][2], grads[1][2]):
+        assert (g0 - g1).abs().max().item() <= 1e-6 * g0.abs().max().item()
