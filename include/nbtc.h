@@ -248,7 +248,12 @@ typedef struct {
   int32_t target_stride;                    /* floats per target texel, >= C (0 means C) */
 } nbtc_train_args;
 
-/* Scratch bytes the training calls need on this context's device. */
+/* Scratch bytes the training calls need on this context's device: the per-CTA
+ * partial sums and one record of 12 + 4 ceil(C / 4) floats per sample, into
+ * which the step first gathers every sample's features and target channels.  A
+ * workspace with room for the partial sums only (one CTA per SM, 48,264 bytes
+ * each) is accepted too: the step then gathers inside its main kernel (same
+ * results, slower). */
 nbtc_status nbtc_train_workspace_bytes(nbtc_context* ctx, const nbtc_train_args* args, size_t* bytes);
 
 /* Forward + loss + backward + Adam (MLP and latents) for one batch.  Writes
