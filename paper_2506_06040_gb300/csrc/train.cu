@@ -261,8 +261,10 @@ __global__ void __launch_bounds__(256) k_gather(TrainDev a, float* __restrict__ 
 // LV: latents and latent gradients hold 4 floats per texel (16-byte texel
 // loads and 16-byte gradient adds); TV: the target's texel stride is a multiple
 // of 4 floats (16-byte loads).  Both give the same arithmetic as the 3-float /
-// scalar forms, in the same order.
-template <int MODE, bool LV, bool TV>
+// scalar forms, in the same order.  CP: output channels as the output layer's
+// products run them (12 for C <= 12, else 16); the channels past C are zero
+// weights and zero deltas, so CP changes no result, only the work.
+template <int MODE, bool LV, bool TV, int CP>
 __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
@@ -386,15 +388,15 @@ __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
     __syncthreads();
     // ---- y = W3 h2 + b3 (thread = sample), loss and dL/dy -> DY
     {
-      float y[kCMax];
+      float y[CP];
 #pragma unroll
-      for (int c = 0; c < kCMax; ++c) y[c] = S.b3[c];
+      for (int c = 0; c < CP; ++c) y[c] = S.b3[c];
 #pragma unroll 4
       for (int k = 0; k < kH; ++k) {
         const float h = S.H2[k * kLd + t];
         const float4* w = reinterpret_cast<const float4*>(S.W3t + k * kCMax);
 #pragma unroll
-        for (int q = 0; q < kCMax / 4; ++q) {
+        for (int q = 0; q < CP / 4; ++q) {
           const float4 wq = w[q];
           y[4 * q + 0] = fmaf(wq.x, h, y[4 * q + 0]);
           y[4 * q + 1] = fmaf(wq.y, h, y[4 * q + 1]);
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
         }
       }
 #pragma unroll
-      for (int c = 0; c < kCMax; ++c) {
+      for (int c = 0; c < CP; ++c) {
         if (c >= C) continue;
         float d = 0.f;
         if (MODE == kModeFwd) {
@@ -429,17 +431,19 @@ __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
     {
       const int ra[1] = {w3c};
       const int rb[4] = {w2i, w2i + 8, w2i + 16, w2i + 24};
-      float d3[1][4];
-      sample_dots<1, 4>(S.DY, ra, S.H2, rb, d3);
+      if (w3c < CP) {  // rows past CP are zero (warps 3 and 7 when CP = 12)
+        float d3[1][4];
+        sample_dots<1, 4>(S.DY, ra, S.H2, rb, d3);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) neumaier(g3s[q], g3e[q], d3[0][q]);
+        for (int q = 0; q < 4; ++q) neumaier(g3s[q], g3e[q], d3[0][q]);
+      }
     }
     float2 acc[4][8];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
-    gemm_8x8<kCMax>(S.DY, S.W3, sg, ng, acc);
+    gemm_8x8<CP>(S.DY, S.W3, sg, ng, acc);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       float2 h[4];
@@ -794,7 +798,7 @@ static nbtc_status pre_gather(nbtc_context* ctx, const nbtc_train_args* A, Train
 
 template <int MODE, bool LV, bool TV>
 static nbtc_status launch_k_train(const TrainDev& d, int grid, cudaStream_t s) {
-  auto kern = k_train<MODE, LV, TV>;
+  auto kern = d.C <= 12 ? k_train<MODE, LV, TV, 12> : k_train<MODE, LV, TV, 16>;
   nbtc_status st = cuda_check(
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)), "smem attr");
   if (st) return st;

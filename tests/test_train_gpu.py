@@ -255,3 +255,24 @@ def test_pre_gathered_and_fused_gather_agree(nb, ctx):
     assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
     for g0, g1 in zip(grads[0][2], grads[1][2]):
         assert (g0 - g1).abs().max().item() <= 1e-6 * g0.abs().max().item()
+
+
+@pytest.mark.parametrize("C,pad", [(3, False), (12, True), (13, True), (16, False), (5, True)])
+def test_channel_counts(nb, ctx, C, pad):
+    """Output widths either side of the kernels' 12 / 16-channel paddings, with
+    plain and padded targets: loss and every gradient against the oracle."""
+    from paper_2506_06040_gb300.train import ContinuousModel, padded
+    rng = synth.Rng(200 + C, 1)
+    sides = [64, 32, 16, 8]
+    lat = [rng.normal(s * s * 3, 0.1).reshape(s, s, 3).astype(np.float32) for s in sides]
+    mlp = synth.he_mlp(synth.Rng(200 + C, 2), [12, 64, 64, C])
+    target = synth.sinusoid_target(synth.Rng(200 + C, 3), 128, channels=C)
+    wl = synth.TrainWorkload("train-C", sides, synth.SHIFTS, lat, mlp, target, 5000 + 13, 200 + C)
+    uv = kink_free(wl, wl.uv(0))
+    model = ContinuousModel.from_synth(wl)
+    tgt = torch.from_numpy(wl.target).cuda()
+    loss = model.train_step(ctx, torch.from_numpy(uv).cuda(), padded(tgt) if pad else tgt)
+    ctx.sync()
+    _, loss_ref, dW, db, dlat = _oracle_grads(wl, uv)
+    assert abs(float(loss.item()) - loss_ref) <= REL * abs(loss_ref)
+    _check_all_grads(model, dW, db, dlat)
