@@ -44,8 +44,8 @@ def decode_grid(material, width: int, height: int, idx=None, precision: str = "f
     if idx is None:
         idx = np.arange(width * height)
     idx = np.asarray(idx, dtype=np.int64)
-    u = (idx % width + 0.5) / width
-    v = (idx // width + 0.5) / height
+    u = sample.grid_coord(idx % width, width).astype(np.float64)
+    v = sample.grid_coord(idx // width, height).astype(np.float64)
     x = features_at(material, u, v, tex)
     return run_mlp(material, x, precision, fp8)
 
@@ -54,8 +54,8 @@ def fp8_calibration(material, width: int, height: int, step: int = 16, tex=None)
     """(sw, sa) power-of-two FP8 scales from the sub-grid of every `step`-th texel."""
     j, i = np.meshgrid(np.arange(0, height, step), np.arange(0, width, step), indexing="ij")
     idx = (j * width + i).reshape(-1)
-    u = (idx % width + 0.5) / width
-    v = (idx // width + 0.5) / height
+    u = sample.grid_coord(idx % width, width).astype(np.float64)
+    v = sample.grid_coord(idx // width, height).astype(np.float64)
     x = features_at(material, u, v, tex)
     acts = mlp.hidden_activations(x, material.mlp.weights, material.mlp.biases)
     return emulate.fp8_scales(material.mlp.weights, acts)

@@ -21,6 +21,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import bc1, emulate
+from . import sample
 from .sample import trilinear
 
 EMPTY, UNIFORM, MIXED = 0, 1, 2
@@ -95,16 +96,9 @@ def level_mips_rgb(level) -> list:
 def _bilinear_bc1(level_blocks, w, h, u, v, shift, address):
     """Bilinear sample of one BC1 mip (w x h) at (u, v), fetching only the four
     texels each sample needs (same filter as sample.bilinear)."""
-    x = np.asarray(u, dtype=np.float64) * w - 0.5 + shift
-    y = np.asarray(v, dtype=np.float64) * h - 0.5 + shift
-    x0, y0 = np.floor(x), np.floor(y)
-    fx, fy = (x - x0)[..., None], (y - y0)[..., None]
-    x0, y0 = x0.astype(np.int64), y0.astype(np.int64)
-    if address == "wrap":
-        xa, xb, ya, yb = np.mod(x0, w), np.mod(x0 + 1, w), np.mod(y0, h), np.mod(y0 + 1, h)
-    else:
-        xa, xb = np.clip(x0, 0, w - 1), np.clip(x0 + 1, 0, w - 1)
-        ya, yb = np.clip(y0, 0, h - 1), np.clip(y0 + 1, 0, h - 1)
+    xa, xb, fx = sample.axis_taps(u, w, shift, address)
+    ya, yb, fy = sample.axis_taps(v, h, shift, address)
+    fx, fy = fx[..., None], fy[..., None]
     t = lambda xx, yy: bc1.texel_rgb8(level_blocks, w, xx, yy).astype(np.float64) / 255.0
     return ((1 - fx) * (1 - fy) * t(xa, ya) + fx * (1 - fy) * t(xb, ya)
             + (1 - fx) * fy * t(xa, yb) + fx * fy * t(xb, yb))

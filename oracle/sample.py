@@ -10,6 +10,14 @@ y (rows), origin at the top-left corner; texel centres sit at half-integers, so
 the continuous texel coordinate is x = u * W - 0.5 + s (s = per-level shift in
 texels, both axes); neighbours x0 = floor(x), x0 + 1 are clamped to [0, W - 1]
 (clamp) or taken modulo W (wrap).
+
+Coordinate precision (a reading: the decode samples at FP32 texture
+coordinates, the uv a shader hands its texture fetch): the texel coordinate x is
+the exact value of u * W - 0.5 + s rounded once to FP32, and a grid's texel-
+centre coordinate is (i + 1/2) / W correctly rounded to FP32.  Which texels are
+read and with which weights is then decided in the same precision as on the
+GPU; the blend and everything after it are FP64.  With power-of-two sizes both
+roundings are exact.
 """
 from __future__ import annotations
 
@@ -24,17 +32,39 @@ def _wrap_or_clamp(i: np.ndarray, n: int, address: str) -> np.ndarray:
     raise ValueError(address)
 
 
+def texel_coord(u, n: int, shift: float) -> np.ndarray:
+    """u * n - 0.5 + shift (exact in FP64 for an FP32 u and n < 2^24) rounded once to FP32."""
+    return (np.asarray(u, dtype=np.float64) * n - 0.5 + shift).astype(np.float32).astype(np.float64)
+
+
+def axis_taps(u, n: int, shift: float, address: str):
+    """Neighbour indices (i0, i1) and weight f of i1 along one axis.  u is taken
+    as FP32; wrap first drops its whole periods (u - floor(u), an FP32
+    subtraction), so tiled coordinates keep their fraction; then the texel
+    coordinate is rounded once to FP32 (texel_coord) and split into floor and
+    fraction (exact); indices are clamped or wrapped as integers."""
+    u = np.asarray(u, dtype=np.float64).astype(np.float32)
+    if address == "wrap":
+        u = u - np.floor(u)
+    x = texel_coord(u.astype(np.float64), n, shift)
+    x0 = np.floor(x)
+    f = x - x0
+    x0 = x0.astype(np.int64)
+    return _wrap_or_clamp(x0, n, address), _wrap_or_clamp(x0 + 1, n, address), f
+
+
+def grid_coord(i, n: int) -> np.ndarray:
+    """Texel-centre coordinate (i + 1/2) / n correctly rounded to FP32 (IEEE FP32 division)."""
+    return (np.asarray(i, dtype=np.float32) + np.float32(0.5)) / np.float32(n)
+
+
 def bilinear(tex: np.ndarray, u, v, shift: float = 0.0, address: str = "clamp") -> np.ndarray:
     """Bilinear sample of tex [H, W, C] (FP64 values) at (u, v); returns [n, C]."""
     tex = np.asarray(tex, dtype=np.float64)
     h, w = tex.shape[:2]
-    x = np.asarray(u, dtype=np.float64) * w - 0.5 + shift
-    y = np.asarray(v, dtype=np.float64) * h - 0.5 + shift
-    x0, y0 = np.floor(x), np.floor(y)
-    fx, fy = (x - x0)[..., None], (y - y0)[..., None]
-    x0, y0 = x0.astype(np.int64), y0.astype(np.int64)
-    xa, xb = _wrap_or_clamp(x0, w, address), _wrap_or_clamp(x0 + 1, w, address)
-    ya, yb = _wrap_or_clamp(y0, h, address), _wrap_or_clamp(y0 + 1, h, address)
+    xa, xb, fx = axis_taps(u, w, shift, address)
+    ya, yb, fy = axis_taps(v, h, shift, address)
+    fx, fy = fx[..., None], fy[..., None]
     return ((1 - fx) * (1 - fy) * tex[ya, xa] + fx * (1 - fy) * tex[ya, xb]
             + (1 - fx) * fy * tex[yb, xa] + fx * fy * tex[yb, xb])
 
@@ -57,9 +87,10 @@ def trilinear(mips: list, u, v, lod, shift: float = 0.0, address: str = "wrap") 
 
 
 def grid_uv(width: int, height: int):
-    """Texel-centre uv of a width x height output, row-major: u = (i + .5)/W, v = (j + .5)/H."""
+    """Texel-centre uv of a width x height output, row-major: u = (i + .5)/W, v = (j + .5)/H
+    (each rounded to FP32, see grid_coord)."""
     j, i = np.meshgrid(np.arange(height), np.arange(width), indexing="ij")
-    return ((i + 0.5) / width).reshape(-1), ((j + 0.5) / height).reshape(-1)
+    return grid_coord(i, width).astype(np.float64).reshape(-1), grid_coord(j, height).astype(np.float64).reshape(-1)
 
 
 def features(level_tex: list, shifts, u, v, address: str = "clamp") -> np.ndarray:

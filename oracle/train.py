@@ -16,18 +16,13 @@ from __future__ import annotations
 
 import numpy as np
 
-from .sample import bilinear
+from .sample import axis_taps, bilinear
 
 
 def _taps(h: int, w: int, u, v, shift: float):
     """Clamp-addressed bilinear taps: four (row, col, weight) triples per sample."""
-    x = np.asarray(u, dtype=np.float64) * w - 0.5 + shift
-    y = np.asarray(v, dtype=np.float64) * h - 0.5 + shift
-    x0, y0 = np.floor(x), np.floor(y)
-    fx, fy = x - x0, y - y0
-    x0, y0 = x0.astype(np.int64), y0.astype(np.int64)
-    xa, xb = np.clip(x0, 0, w - 1), np.clip(x0 + 1, 0, w - 1)
-    ya, yb = np.clip(y0, 0, h - 1), np.clip(y0 + 1, 0, h - 1)
+    xa, xb, fx = axis_taps(u, w, shift, "clamp")
+    ya, yb, fy = axis_taps(v, h, shift, "clamp")
     return [(ya, xa, (1 - fx) * (1 - fy)), (ya, xb, fx * (1 - fy)),
             (yb, xa, (1 - fx) * fy), (yb, xb, fx * fy)]
 

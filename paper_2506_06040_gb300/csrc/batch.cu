@@ -470,8 +470,8 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     d.d.grid_w = M.out ? M.out_w : 0;
     d.d.grid_h = M.out ? M.out_h : 0;
     d.d.n = M.out ? (int64_t)M.out_w * M.out_h : 0;
-    d.d.inv_gw = M.out ? 1.0f / (float)M.out_w : 0.f;
-    d.d.inv_gh = M.out ? 1.0f / (float)M.out_h : 0.f;
+    d.d.cw = make_grid_coord(M.out ? M.out_w : 1);
+    d.d.ch = make_grid_coord(M.out ? M.out_h : 1);
     d.d.out = M.out;
     d.d.status = ctx->status_dev;
     d.packed = B->packed_dev + B->packed_stride * m;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/nbtc.h"
+#include "gridcoord.h"
 
 namespace nbtc {
 
@@ -88,16 +89,12 @@ __device__ __forceinline__ void axis_taps(float u, int n, float shift, bool wrap
   // coordinate keeps its fraction even for tiled uv far from [0, 1)
   if (wrap) u -= floorf(u);
   float t = fmaf(u, (float)n, shift - 0.5f);
-  if (wrap) {
-    t -= (float)n * floorf(t / (float)n);  // into [0, n)
-  } else {
-    t = fminf(fmaxf(t, -1.0f), (float)n);  // outside this range clamping decides
-  }
+  if (!wrap) t = fminf(fmaxf(t, -1.0f), (float)n);  // outside this range clamping decides
   const float fl = floorf(t);
-  f = t - fl;
+  f = t - fl;  // exact
   const int a = (int)fl;
-  if (wrap) {
-    i0 = a >= n ? a - n : a;
+  if (wrap) {  // u in [0, 1] and |shift| <= 1/2: a in [-1, n], wrapped as an integer
+    i0 = a < 0 ? a + n : (a >= n ? a - n : a);
     i1 = i0 + 1 >= n ? i0 + 1 - n : i0 + 1;
   } else {
     i0 = min(max(a, 0), n - 1);
@@ -135,7 +132,7 @@ struct DecodeArgs {
   int64_t n;
   int32_t grid_w, grid_h;  // grid mode: texels per row, rows decoded by this call
   int32_t row0;            // grid mode: first row (of the full grid) decoded by this call
-  float inv_gw, inv_gh;    // grid mode: 1 / width, 1 / height of the full grid
+  GridCoord cw, ch;        // grid mode: width and height of the full grid (texel-centre coordinates)
   void* out;
   int* status;
 };
@@ -152,7 +149,7 @@ __device__ __forceinline__ float2 texel_uv(const DecodeArgs& a, int64_t t) {
     j = t / a.grid_w;
     i = t - j * a.grid_w;
   }
-  return make_float2(((float)i + 0.5f) * a.inv_gw, ((float)(j + a.row0) + 0.5f) * a.inv_gh);
+  return make_float2(grid_coord((float)i, a.cw), grid_coord((float)(j + a.row0), a.ch));
 }
 
 }  // namespace nbtc

@@ -203,8 +203,8 @@ static nbtc_status make_decode_args(nbtc_context* ctx, const nbtc_latents* lat, 
   a.n = n;
   a.grid_w = grid_w;
   a.grid_h = grid_h;
-  a.inv_gw = uv ? 0.f : 1.0f / (float)grid_w;
-  a.inv_gh = uv ? 0.f : 1.0f / (float)grid_h;
+  a.cw = make_grid_coord(uv ? 1 : grid_w);
+  a.ch = make_grid_coord(uv ? 1 : grid_h);
   a.out = out;
   a.status = ctx->status_dev;
   return NBTC_OK;
@@ -277,7 +277,7 @@ nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const n
   if (rows == 0) return NBTC_OK;
   if ((st = resolve_out(precision, a))) return st;
   a.row0 = row0;
-  a.inv_gh = 1.0f / (float)grid_h;
+  a.ch = make_grid_coord(grid_h);
   switch (precision) {
     case NBTC_FP32:
       return launch_decode_fp32(ctx, a, mlp, (cudaStream_t)stream);

@@ -63,8 +63,8 @@ __device__ __forceinline__ TilePlan plan_tile(const DecodeArgs& a, int64_t tile_
     P.j = (int)(tile_start / a.grid_w);
     P.i0 = (int)(tile_start - (int64_t)P.j * a.grid_w);
   }
-  const float u0 = ((float)P.i0 + 0.5f) * a.inv_gw;
-  const float u1 = ((float)(P.i0 + NT - 1) + 0.5f) * a.inv_gw;
+  const float u0 = grid_coord((float)P.i0, a.cw);
+  const float u1 = grid_coord((float)(P.i0 + NT - 1), a.cw);
   int total = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -91,7 +91,7 @@ __device__ __forceinline__ ColumnJob column_job(const DecodeArgs& a, const TileP
   J.k = (job >= P.pre[1]) + (job >= P.pre[2]) + (job >= P.pre[3]);
   J.rel = job - pick4(P.pre, J.k);
   const LevelView& L = a.lv[J.k];
-  const float v = ((float)(P.j + a.row0) + 0.5f) * a.inv_gh;
+  const float v = grid_coord((float)(P.j + a.row0), a.ch);
   const float ty = texel_coord(v, L.h, L.shift);
   const float fty = floorf(ty);
   J.fy = ty - fty;
@@ -148,7 +148,7 @@ __device__ __forceinline__ void decode_columns(const DecodeArgs& a, const TilePl
 template <int NT>
 __device__ __forceinline__ void blend_columns(const DecodeArgs& a, const TilePlan& P, int tid, const float4* colbuf,
                                               float (&feat)[12]) {
-  const float u = ((float)(P.i0 + tid) + 0.5f) * a.inv_gw;
+  const float u = grid_coord((float)(P.i0 + tid), a.cw);
   const float s = 1.0f / 255.0f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -211,9 +211,9 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
   if (i0 != C.i0) {  // new strip: column plan, own job, own texel's taps
     C.i0 = i0;
     C.key = INT_MIN + 1;  // no pair decoded (and key == C.key + 1 cannot hold)
-    const float u0 = ((float)i0 + 0.5f) * a.inv_gw;
-    const float u1 = ((float)(i0 + NT - 1) + 0.5f) * a.inv_gw;
-    const float u = ((float)(i0 + tid) + 0.5f) * a.inv_gw;
+    const float u0 = grid_coord((float)i0, a.cw);
+    const float u1 = grid_coord((float)(i0 + NT - 1), a.cw);
+    const float u = grid_coord((float)(i0 + tid), a.cw);
     int total = 0, job = -1, jx = 0;
     uint32_t rel4 = 0;
 #pragma unroll
@@ -241,7 +241,7 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
   if (C.job >= 0) {
     const int k = C.job & 3;
     const LevelView& L = a.lv[k];
-    const float ty = texel_coord(((float)(j + a.row0) + 0.5f) * a.inv_gh, L.h, L.shift);
+    const float ty = texel_coord(grid_coord((float)(j + a.row0), a.ch), L.h, L.shift);
     const float fty = floorf(ty);
     const float fy = ty - fty;
     const int key = (int)fty;
@@ -270,7 +270,7 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
     sm100::sts128f(colbuf + 16u * (uint32_t)(k * kColCap + (C.job >> 2)), fmaf(fy, C.dc[0], C.c0[0]),
                    fmaf(fy, C.dc[1], C.c0[1]), fmaf(fy, C.dc[2], C.c0[2]), 0.f);
     // the next row's pair changes here too: start pulling its blocks into L1
-    const float tyn = texel_coord(((float)(j + a.row0) + 1.5f) * a.inv_gh, L.h, L.shift);
+    const float tyn = texel_coord(grid_coord((float)(j + a.row0 + 1), a.ch), L.h, L.shift);
     const int keyn = (int)floorf(tyn);
     if (keyn != key && j + 1 < a.grid_h) {
       const int y1 = wrap_or_clamp(keyn + 1, L.h, a.wrap);

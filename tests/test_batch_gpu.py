@@ -40,7 +40,7 @@ def ctx(nb):
 
 
 def _grid_check(mat, S, got, idx):
-    uv = np.stack([(idx % S + 0.5) / S, (idx // S + 0.5) / S], -1)
+    uv = np.stack([oracle.sample.grid_coord(idx % S, S), oracle.sample.grid_coord(idx // S, S)], -1).astype(np.float64)
     lod = np.full(len(idx), -64.0)   # mip 0 of every level
     emu = oracle.frame.decode_pixels_direct(mat, uv, lod, "fp16")
     _check(got, emu, mat, FEATURE_BOUND(len(idx)), 2.0 ** -10, FRAC)

@@ -12,6 +12,12 @@ from gpu_util import require_gpu
 pytestmark = pytest.mark.gpu
 
 
+def _grid_uv(idx, gw, gh):
+    """Texel-centre uv of grid indices, FP32 as the decode forms them."""
+    return (oracle.sample.grid_coord(idx % gw, gw).astype(np.float64),
+            oracle.sample.grid_coord(idx // gw, gh).astype(np.float64))
+
+
 def ulp16(x):
     """Spacing of binary16 numbers at |x| (2^-24 below the normal range)."""
     ax = np.maximum(np.abs(np.asarray(x, dtype=np.float64)), 2.0 ** -14)
@@ -80,7 +86,8 @@ def _check_fp16(got, emu, material, x):
 def _grid_x(material, gw, gh, idx=None):
     if idx is None:
         idx = np.arange(gw * gh)
-    return oracle.decode.features_at(material, (idx % gw + 0.5) / gw, (idx // gw + 0.5) / gh)
+    return oracle.decode.features_at(material, oracle.sample.grid_coord(idx % gw, gw).astype(np.float64),
+                                     oracle.sample.grid_coord(idx // gw, gh).astype(np.float64))
 
 
 @pytest.mark.parametrize("dims", [[12, 64, 9], [12, 64, 64, 9], [12, 64, 64, 64, 9]])
@@ -140,7 +147,7 @@ def test_fp16_full_size_sampled_and_error_budget(nb, ctx):
     got = y[torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
     tex = [oracle.decode.level_rgb(lv) for lv in wl.material.levels]
     emu = oracle.decode.decode_grid(wl.material, 4096, 4096, idx, precision="fp16", tex=tex)
-    x = oracle.decode.features_at(wl.material, (idx % 4096 + 0.5) / 4096, (idx // 4096 + 0.5) / 4096, tex)
+    x = oracle.decode.features_at(wl.material, *_grid_uv(idx, 4096, 4096), tex)
     e_emu, frac = _check_fp16(got, emu, wl.material, x)
     ref = oracle.decode.decode_grid(wl.material, 4096, 4096, idx, tex=tex)
     per_channel = np.abs(got - ref).max(axis=0)
@@ -206,7 +213,7 @@ def test_fp8_full_size_sampled(nb, ctx):
     got = y[torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
     tex = [oracle.decode.level_rgb(lv) for lv in wl.material.levels]
     emu = oracle.decode.decode_grid(wl.material, 4096, 4096, idx, precision="fp8", fp8=scales, tex=tex)
-    x = oracle.decode.features_at(wl.material, (idx % 4096 + 0.5) / 4096, (idx // 4096 + 0.5) / 4096, tex)
+    x = oracle.decode.features_at(wl.material, *_grid_uv(idx, 4096, 4096), tex)
     _check(got, emu, wl.material, x, 2.0 ** -3, 0.99)
 
 

@@ -19,8 +19,11 @@ def _scipy_bilinear(tex, u, v, shift, mode):
 def test_bilinear_matches_scipy(shift, address, mode):
     rng = np.random.default_rng(3)
     tex = rng.random((8, 16, 3))
-    u = rng.uniform(-0.3, 1.3, 4000)
-    v = rng.uniform(-0.3, 1.3, 4000)
+    # coordinates on a 2^-12 grid: exact in FP32, so dropping whole periods (wrap)
+    # and forming the texel coordinate lose nothing and the FP64 interpolation
+    # must match scipy's
+    u = rng.integers(-1229, 5325, 4000) / 4096.0
+    v = rng.integers(-1229, 5325, 4000) / 4096.0
     got = sample.bilinear(tex, u, v, shift, address)
     want = _scipy_bilinear(tex, u, v, shift, mode)
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
@@ -84,3 +87,53 @@ def test_grid_uv_row_major():
     u, v = sample.grid_uv(4, 2)
     np.testing.assert_allclose(u, [0.125, 0.375, 0.625, 0.875] * 2)
     np.testing.assert_allclose(v, [0.25] * 4 + [0.75] * 4)
+
+
+def test_grid_coord_is_the_correctly_rounded_quotient():
+    """grid_coord(i, n) is (2i + 1) / (2n) rounded to the nearest FP32 (ties to
+    even), checked against exact rational arithmetic; exact for powers of two."""
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    for n in (200, 1000, 3840, 1731, 4096, 7):
+        idx = rng.integers(0, n, 300)
+        got = sample.grid_coord(idx, n)
+        assert got.dtype == np.float32
+        for i, g in zip(idx, got):
+            exact = Fraction(2 * int(i) + 1, 2 * n)
+            g_f = Fraction(float(g))
+            lo = Fraction(float(np.nextafter(g, np.float32(-1))))
+            hi = Fraction(float(np.nextafter(g, np.float32(2))))
+            # no FP32 neighbour is closer to the exact value
+            assert abs(g_f - exact) <= abs(lo - exact) and abs(g_f - exact) <= abs(hi - exact)
+            if n & (n - 1) == 0:
+                assert g_f == exact
+
+
+def test_texel_coord_rounds_once_to_fp32():
+    """texel_coord = u n - 1/2 + s rounded once: exact for power-of-two n and an
+    FP32 u; for other n it is the FP32 value nearest the exact one."""
+    from fractions import Fraction
+    rng = np.random.default_rng(12)
+    u = rng.uniform(0, 1, 500).astype(np.float32)
+    for n, s in ((1024, 0.5), (384, 0.0), (1000, 0.5)):
+        x = sample.texel_coord(u.astype(np.float64), n, s)
+        for ui, xi in zip(u, x):
+            exact = Fraction(float(ui)) * n - Fraction(1, 2) + Fraction(s)
+            if n & (n - 1) == 0:
+                assert Fraction(xi) == exact
+            else:
+                xf = np.float32(xi)
+                assert abs(Fraction(xi) - exact) <= abs(Fraction(float(np.nextafter(xf, np.float32(-1e9)))) - exact)
+                assert abs(Fraction(xi) - exact) <= abs(Fraction(float(np.nextafter(xf, np.float32(1e9)))) - exact)
+
+
+def test_wrap_is_periodic():
+    """Wrap addressing: shifting u, v by whole periods changes nothing (coordinates
+    on a 2^-12 grid, periods up to 8 as in the tiled frame)."""
+    rng = np.random.default_rng(13)
+    tex = rng.random((16, 32, 3))
+    u = rng.integers(0, 4096, 1000) / 4096.0
+    v = rng.integers(0, 4096, 1000) / 4096.0
+    base = sample.bilinear(tex, u, v, 0.5, "wrap")
+    for k in (-3, 1, 7):
+        np.testing.assert_array_equal(sample.bilinear(tex, u + k, v - k, 0.5, "wrap"), base)
