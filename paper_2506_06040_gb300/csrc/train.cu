@@ -116,7 +116,7 @@ __device__ __forceinline__ void load_samples(const float* __restrict__ row, int 
 template <int K>
 __device__ __forceinline__ void gemm_8x8(const float* __restrict__ A, const float* __restrict__ Bm, int sg, int ng,
                                          float2 (&acc)[4][8]) {
-#pragma unroll 2
+#pragma unroll 8
   for (int k = 0; k < K; ++k) {
     float2 av[4];
     load_samples(A + k * kLd, sg, av);
@@ -152,7 +152,7 @@ __device__ __forceinline__ void sample_dots(const float* __restrict__ A, const i
   for (int i = 0; i < NA; ++i)
 #pragma unroll
     for (int j = 0; j < NB; ++j) acc[i][j] = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll 8
   for (int s = 0; s < kTS; s += 4) {
     float4 av[NA], bv[NB];
 #pragma unroll
