@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kTW, 1) k_decode_fp32_wide(DecodeArgs a, const
         dg[c] = *reinterpret_cast<const float2*>(S.b + NHID * kD + 2 * c);
         ad[c] = *reinterpret_cast<const float2*>(S.bs + NHID * kD + 2 * c);
       }
-#pragma unroll 4
+#pragma unroll 8
       for (int k = 0; k < kD; ++k) {
         const float2 hv = *reinterpret_cast<const float2*>(Hb + k * TW + 2 * lt);
         const float2* wn = reinterpret_cast<const float2*>(S.won + k * kOutMax);
