@@ -48,6 +48,15 @@ def _peaks() -> dict:
             "source": "fallback"}
 
 
+def _hbm(algo_bytes: int, ms: float, peaks: dict) -> dict:
+    """The same launch against the HBM roofline: algorithmic bytes (output stream
+    + BC1 blocks + MLP) over the kernel time, against the measured copy bandwidth."""
+    gbs = algo_bytes / (ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "algorithmic_bytes": int(algo_bytes),
+            "peak_source": peaks.get("source", "fallback") + " copy bandwidth"}
+
+
 def _profiled_traffic(profile: str):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
     kernel, as recorded in profiles/<profile>.md from one ncu capture, or None
@@ -232,10 +241,12 @@ def run_forms(args, nb, ctx, stream, flush, peaks, sm_count) -> dict:
         ms = statistics.mean(t)
         err = (out16.float() - out32).abs().amax(dim=0).tolist()
         ach = flop * n / (ms * 1e-3) / 1e12
+        algo = n * mat.n_out * 2 + sum(b.numel() * 8 for b in mat.blocks) + packed.numel() * packed.element_size()
         res[name] = {"gtexel_s": n / ms / 1e6, "kernel_ms": ms, "max_abs_dev_vs_fp32_per_channel": err,
                      "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                                   "frac": ach / peak, "traffic": _profiled_traffic(f"k_decode_tc_{name.split('_')[0]}_{W}sq"),
-                                  "peak_source": "measured bf16 dense burst" + (" x 2 (fp8 nominal ratio)" if prec == nb.FP8_E4M3 else "")}}
+                                  "peak_source": "measured bf16 dense burst" + (" x 2 (fp8 nominal ratio)" if prec == nb.FP8_E4M3 else ""),
+                                  "hbm": _hbm(algo, ms, peaks)}}
     res["fp16_tc_speedup_vs_fp32"] = res["fp16_tc"]["gtexel_s"] / res["fp32"]["gtexel_s"]
     ctx.sync(stream)
     return res
@@ -443,7 +454,9 @@ def run_ours(args) -> dict | None:
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_tf, "traffic": _profiled_traffic("k_decode_fp32_wide_4096sq"),
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
-                     "kernel": "k_decode_fp32_wide<2, 2>", "kernel_ms": kernel_ms},
+                     "kernel": "k_decode_fp32_wide<2, 2>", "kernel_ms": kernel_ms,
+                     "hbm": _hbm(n * 9 * 4 + sum(b.numel() * 8 for b in mat.blocks) +
+                                 (mat.weights.numel() + mat.biases.numel()) * 4, kernel_ms, peaks)},
         "e2e": {"value": e2e, "unit": "Gtexel/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clk,
