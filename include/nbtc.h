@@ -125,8 +125,14 @@ const char* nbtc_status_string(nbtc_status s);
 /* Message describing the last non-OK return on the calling thread ("" if none). */
 const char* nbtc_last_error(void);
 
-/* Tests only: caps every device-side bounded wait of this context at
- * `spins` iterations (0 restores the default budget). */
+/* Tests only: caps the device-side bounded waits of this context's decode
+ * loops at `spins` polls (0 restores the default budget; -1 makes every such
+ * wait exceed it at once).  A wait past its budget records NBTC_ERR_TIMEOUT in
+ * the status word (the launch's results are void) and then keeps waiting with
+ * a fixed budget (2^22 polls of <= 1 us), so the kernel's hand-offs stay in
+ * step and it releases its resources only after its own tensor-core work and
+ * bulk copies have finished; the context stays usable.  Waits that guard
+ * resources (weight loads, the final drain) always use the fixed budget. */
 nbtc_status nbtc_set_wait_budget(nbtc_context* ctx, int64_t spins);
 
 /* ------------------------------------------------------------------ decode */

@@ -228,7 +228,7 @@ static TcArgs base_args(nbtc_context* ctx, const nbtc_batch* B) {
   TcArgs p;
   memset(&p, 0, sizeof(p));
   p.d.status = ctx->status_dev;
-  p.budget = ctx->wait_budget > 0 ? ctx->wait_budget : kDefaultWaitBudget;
+  p.budget = ctx->wait_budget > 0 ? ctx->wait_budget : ctx->wait_budget < 0 ? 0 : kDefaultWaitBudget;
   p.mode = kModeBatch;
   p.mats = B->mats_dev;
   return p;

@@ -156,7 +156,7 @@ const char* nbtc_last_error(void) { return g_last_error.c_str(); }
 
 nbtc_status nbtc_set_wait_budget(nbtc_context* ctx, int64_t spins) {
   if (!ctx) return fail(NBTC_ERR_INVALID_ARG, "context is NULL");
-  if (spins < 0) return fail(NBTC_ERR_INVALID_ARG, "spins must be >= 0");
+  if (spins < -1) return fail(NBTC_ERR_INVALID_ARG, "spins must be >= -1");
   ctx->wait_budget = spins;
   return NBTC_OK;
 }

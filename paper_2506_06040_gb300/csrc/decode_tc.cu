@@ -188,7 +188,7 @@ nbtc_status launch_decode_tc(nbtc_context* ctx, const DecodeArgs& a, const nbtc_
   p.packed = packed;
   p.nout = mlp->dims[nhid + 1];
   p.tiles = (a.n + kTile - 1) / kTile;
-  p.budget = ctx->wait_budget > 0 ? ctx->wait_budget : kDefaultWaitBudget;
+  p.budget = ctx->wait_budget > 0 ? ctx->wait_budget : ctx->wait_budget < 0 ? 0 : kDefaultWaitBudget;
   bool fp = a.uv == nullptr && (a.grid_w % kTile) == 0;
   for (int k = 0; k < 4; ++k) fp = fp && a.lv[k].w <= a.grid_w;
   p.footprint = fp ? 1 : 0;

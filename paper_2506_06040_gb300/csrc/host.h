@@ -11,7 +11,7 @@ struct nbtc_context {
   int device = 0;
   int sm_count = 0;
   int* status_dev = nullptr;       // device status word (first recorded fault)
-  long long wait_budget = 0;       // spins per bounded device wait (0 = default)
+  long long wait_budget = 0;       // spins per bounded device wait (0 = default, -1 = give up at once)
   int tc_groups = 4;               // warpgroups per CTA of the tensor-core decode (3 or 4)
   int fp32_groups = 2;             // independent thread groups per CTA of the FP32 wide decode (1 or 2)
 };

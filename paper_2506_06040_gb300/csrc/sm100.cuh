@@ -58,6 +58,11 @@ constexpr uint32_t kWaitHintNs = 1000;
 // Bounded wait for phase `parity` of an mbarrier: false when `budget` polls
 // (each sleeping up to kWaitHintNs) passed without completion; the caller then
 // records a timeout and winds down.
+// Budget of the waits that must end before a kernel may release its resources
+// (weights loaded by bulk copy, the final drain of the MMAs): never the
+// shortened test budget.
+constexpr long long kDrainBudget = 1ll << 22;
+
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long budget) {
   for (long long i = 0; i < budget; ++i)
     if (mbar_try_wait_hint(bar, parity, kWaitHintNs)) return true;

@@ -60,7 +60,7 @@ struct TcSmem {
   int slot;        // bytes per slot
   int a0, ah;      // offsets inside a slot
   int stage;       // per-warp output staging
-  int bars;        // A-ready[NS], D-ready[NS], weight barrier
+  int bars;        // D-ready[NS], weight barrier, MMA-warp drain[W] (room for 2 NS + 1)
   int tslot;       // TMEM address slot
   int work;        // TcWork
   int total;
@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   if (tid == 0) {
     for (int q = 0; q < NS; ++q) mbar_init(dbar0 + q * 8, 1);
     mbar_init(wbar, 1);
+    for (int m = 0; m < W; ++m) mbar_init(wbar + 8 + m * 8, 1);  // drain barriers
     fence_mbar_init();
     work.m.packed = nullptr;
     work.c.mat = -1;
@@ -188,7 +189,9 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
     first_chunk = false;
     if (!work.valid) break;
     if (work.reload) {
-      if (!failed) failed = !mbar_wait_bounded(wbar, wph, p.budget);
+      // always waited (fixed budget), also after a timed-out D-ready wait: the
+      // copy must land before the MMAs read the image and before the CTA exits
+      if (!mbar_wait_bounded(wbar, wph, kDrainBudget)) failed = true;
       wph ^= 1u;
     }
     failed = __syncthreads_or(failed);
@@ -456,7 +459,13 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
           for (int s = 0; s < kSlots; ++s) {
             if (s == 1 && !two) break;
             const int q = wg * kSlots + s;
-            if (!failed) failed = !mbar_wait_bounded(dbar0 + q * 8, dph[s], p.budget);
+            // past the budget: record the timeout, then keep waiting (fixed budget)
+            // so the warpgroup never runs ahead of its MMA warp -- running ahead
+            // would arrive twice on one A-ready named barrier before it completes
+            if (!mbar_wait_bounded(dbar0 + q * 8, dph[s], p.budget)) {
+              failed = true;
+              mbar_wait_bounded(dbar0 + q * 8, dph[s], kDrainBudget);
+            }
             dph[s] ^= 1u;
             failed = __any_sync(0xffffffffu, failed);  // one failure state per warp
             tc_fence_after();
@@ -476,7 +485,15 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
     __syncthreads();
     tc_fence_after();
   }
-  if (failed && tid == 0) record_status(status, NBTC_ERR_TIMEOUT);
+  // Drain: the issuing lane of each MMA warp commits once more and waits for it
+  // (drain budget), so that TMEM is released only after every MMA it issued has
+  // completed -- also when a D-ready wait gave up and the warpgroup ran ahead.
+  if (warp >= 4 * W && lane == 0) {
+    const uint32_t db = wbar + 8 + (warp - 4 * W) * 8;
+    mma_commit(db);
+    if (!mbar_wait_bounded(db, 0, kDrainBudget)) failed = true;
+  }
+  if (failed) record_status(status, NBTC_ERR_TIMEOUT);
   bulk_wait0();  // this thread's bulk output copies (if any) are complete
   tc_fence_before();
   __syncthreads();

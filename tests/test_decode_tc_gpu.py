@@ -238,3 +238,44 @@ def test_packed_sizes(nb, ctx):
     with pytest.raises(nb.NbtcError):
         api.packed_mlp_bytes(nb.Material.from_synth(synth.small_decode_workload(256, [12, 48, 9], seed=5).material),
                              nb.FP16)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_forced_timeout_reports_status_and_context_recovers(nb, ctx, batched):
+    """Every bounded wait of the decode loop gives up at once (test budget -1):
+    the launch completes, records NBTC_ERR_TIMEOUT in the context's status word
+    and the next sync reports it (once); with the budget restored the same
+    context decodes correctly again.  Single-material launches read the budget
+    per call; a batch plan bakes it into its graph when it is created."""
+    from paper_2506_06040_gb300 import _abi
+    if batched:
+        mats = [nb.Material.from_synth(synth.small_decode_workload(256, [12, 64, 64, 9], seed=45 + i).material)
+                for i in range(3)]
+        outs = [(torch.empty((256 * 256, 9), dtype=torch.float16, device="cuda"), 256, 256) for _ in mats]
+        make = lambda: nb.Batch(ctx, mats, outs, autotune=False)
+        result = lambda: torch.cat([o[0] for o in outs])
+    else:
+        wl = synth.small_decode_workload(512, [12, 64, 64, 64, 9], seed=44)
+        mat = nb.Material.from_synth(wl.material)
+        packed = nb.pack_mlp(ctx, mat, nb.FP16)
+        out = torch.empty((512 * 64, 9), dtype=torch.float16, device="cuda")
+
+        class _Single:
+            def decode(self):
+                nb.decode(ctx, mat, nb.FP16, packed, grid=(512, 64), out=out)
+        make = _Single
+        result = lambda: out
+    make().decode()
+    ctx.sync()
+    ref = result().clone()
+    ctx.set_wait_budget(-1)
+    try:
+        make().decode()
+        assert ctx.status() == _abi.ERR_TIMEOUT
+        assert ctx.status() == _abi.OK   # reported once, then cleared
+    finally:
+        ctx.set_wait_budget(0)
+    result().zero_()
+    make().decode()
+    ctx.sync()
+    assert torch.equal(result().view(torch.int16), ref.view(torch.int16))
