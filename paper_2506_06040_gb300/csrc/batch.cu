@@ -397,6 +397,7 @@ extern "C" {
 
 nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats, int32_t count,
                               const nbtc_frame* frame, int32_t flags, nbtc_batch** plan, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if (!plan || !mats || count < 1 || count > kMaxMaterials)
@@ -600,6 +601,7 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
 }
 
 nbtc_status nbtc_decode_batched(nbtc_context* ctx, nbtc_batch* B, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if (!B) return fail(NBTC_ERR_INVALID_ARG, "plan NULL");
@@ -608,6 +610,7 @@ nbtc_status nbtc_decode_batched(nbtc_context* ctx, nbtc_batch* B, void* stream) 
 }
 
 nbtc_status nbtc_render_frame(nbtc_context* ctx, nbtc_batch* B, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if (!B) return fail(NBTC_ERR_INVALID_ARG, "plan NULL");

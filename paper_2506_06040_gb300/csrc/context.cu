@@ -163,6 +163,7 @@ nbtc_status nbtc_set_wait_budget(nbtc_context* ctx, int64_t spins) {
 
 nbtc_status nbtc_bc1_decode_level(nbtc_context* ctx, const nbtc_level* level, int32_t mip,
                                   uint8_t* out_dev, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if (!level || !out_dev) return fail(NBTC_ERR_INVALID_ARG, "level or out is NULL");
@@ -213,6 +214,7 @@ static nbtc_status make_decode_args(nbtc_context* ctx, const nbtc_latents* lat, 
 nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp,
                                int32_t grid_w, int32_t grid_h, int32_t step, float* act_absmax_dev,
                                void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if (step < 1) return fail(NBTC_ERR_INVALID_ARG, "step must be >= 1");
@@ -248,6 +250,7 @@ static nbtc_status resolve_out(int32_t precision, DecodeArgs& a) {
 nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp, int32_t precision,
                         const void* packed_dev, const float* uv_dev, int64_t n, int32_t grid_w,
                         int32_t grid_h, void* out_dev, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   DecodeArgs a;
@@ -268,6 +271,7 @@ nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_m
 nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_mlp* mlp, int32_t precision,
                              const void* packed_dev, int32_t grid_w, int32_t grid_h, int32_t row0, int32_t rows,
                              void* out_dev, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if (grid_h <= 0 || row0 < 0 || rows < 0 || row0 > grid_h || rows > grid_h - row0)
@@ -304,6 +308,7 @@ nbtc_status nbtc_packed_mlp_bytes(const nbtc_mlp* mlp, int32_t precision, size_t
 nbtc_status nbtc_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int32_t precision,
                           const float* act_absmax_dev, void* packed_dev, size_t packed_bytes,
                           void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if ((st = check_mlp(mlp))) return st;
@@ -319,6 +324,7 @@ nbtc_status nbtc_train_workspace_bytes(nbtc_context* ctx, const nbtc_train_args*
 }
 
 nbtc_status nbtc_train_step(nbtc_context* ctx, const nbtc_train_args* args, float* loss_dev, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if (!args) return fail(NBTC_ERR_INVALID_ARG, "args NULL");
@@ -327,12 +333,14 @@ nbtc_status nbtc_train_step(nbtc_context* ctx, const nbtc_train_args* args, floa
 }
 
 nbtc_status nbtc_qat_decode(nbtc_context* ctx, const nbtc_qat_level* level, float* out, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   return qat_decode(ctx, level, out, (cudaStream_t)stream);
 }
 
 nbtc_status nbtc_qat_encode(nbtc_context* ctx, const nbtc_qat_level* level, uint64_t* blocks, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   return qat_encode(ctx, level, blocks, (cudaStream_t)stream);
@@ -340,12 +348,14 @@ nbtc_status nbtc_qat_encode(nbtc_context* ctx, const nbtc_qat_level* level, uint
 
 nbtc_status nbtc_train_step_qat(nbtc_context* ctx, const nbtc_train_args* args, const nbtc_qat_level* levels,
                                 float* loss_dev, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   return train_step_qat(ctx, args, levels, loss_dev, (cudaStream_t)stream);
 }
 
 nbtc_status nbtc_forward_continuous(nbtc_context* ctx, const nbtc_train_args* args, float* y_dev, void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if (!args) return fail(NBTC_ERR_INVALID_ARG, "args NULL");
@@ -354,6 +364,7 @@ nbtc_status nbtc_forward_continuous(nbtc_context* ctx, const nbtc_train_args* ar
 
 nbtc_status nbtc_backward_continuous(nbtc_context* ctx, const nbtc_train_args* args, const float* dy_dev,
                                      void* stream) {
+  NBTC_RANGE();
   nbtc_status st = enter(ctx);
   if (st) return st;
   if (!args) return fail(NBTC_ERR_INVALID_ARG, "args NULL");

@@ -16,7 +16,20 @@ struct nbtc_context {
   int fp32_groups = 2;             // independent thread groups per CTA of the FP32 wide decode (1 or 2)
 };
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace nbtc {
+
+// Names a C-ABI call in profiler timelines: an NVTX range for the call's
+// duration on the host (nothing happens unless a profiler is attached).
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+  CallRange(const CallRange&) = delete;
+  CallRange& operator=(const CallRange&) = delete;
+};
+#define NBTC_RANGE() ::nbtc::CallRange nbtc_call_range_(__func__)
+
 
 // Records `msg` as the calling thread's last error and returns `code`.
 nbtc_status fail(nbtc_status code, const std::string& msg);

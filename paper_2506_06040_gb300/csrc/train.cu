@@ -920,6 +920,7 @@ void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 }  // namespace nbtc
 
 extern "C" nbtc_status nbtc_train_step_noalloc(const nbtc_train_args* args, float* loss_dev, void* stream) {
+  NBTC_RANGE();
   using namespace nbtc;
   if (!args) return fail(NBTC_ERR_INVALID_ARG, "args NULL");
   int dev = 0;

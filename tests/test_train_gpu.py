@@ -276,3 +276,30 @@ def test_channel_counts(nb, ctx, C, pad):
     _, loss_ref, dW, db, dlat = _oracle_grads(wl, uv)
     assert abs(float(loss.item()) - loss_ref) <= REL * abs(loss_ref)
     _check_all_grads(model, dW, db, dlat)
+
+
+def test_resume_from_checkpoint(nb, ctx, tmp_path):
+    """Two steps, save, one more step -- against load and one step: the resumed
+    step starts from exactly the saved state, so its loss and MLP update are
+    bit-identical (deterministic sums); the latent update matches up to the
+    order of the gradient's atomic adds."""
+    from paper_2506_06040_gb300 import checkpoint
+    from paper_2506_06040_gb300.train import ContinuousModel, padded
+    wl = _mid_workload(seed=80)
+    tgt = padded(torch.from_numpy(wl.target).cuda())
+    a = ContinuousModel.from_synth(wl)
+    for i in range(2):
+        a.train_step(ctx, torch.from_numpy(wl.uv(i)).cuda(), tgt)
+    path = str(tmp_path / "state.ckpt")
+    checkpoint.save(a, path)
+    b = checkpoint.load(path)
+    uv = torch.from_numpy(wl.uv(2)).cuda()
+    la = a.train_step(ctx, uv, tgt)
+    lb = b.train_step(ctx, uv, tgt)
+    ctx.sync()
+    assert torch.equal(la, lb)
+    assert torch.equal(a.weights, b.weights) and torch.equal(a.biases, b.biases)
+    assert torch.equal(a.m_w, b.m_w) and torch.equal(a.v_w, b.v_w)
+    for k in range(4):
+        assert (a.latents[k] - b.latents[k]).abs().max().item() <= 1e-6
+    assert a.step_count == b.step_count == 3
