@@ -69,7 +69,7 @@ def test_decode_ragged_grids(nb, ctx, gw, gh):
     assert max_abs(y.cpu().numpy(), ref) <= TOL_FP32
 
 
-@pytest.mark.parametrize("gw,gh", [(200, 136), (333, 3), (1, 1), (768, 5), (4096, 2), (1280, 9)])
+@pytest.mark.parametrize("gw,gh", [(200, 136), (333, 3), (1, 1), (768, 5), (4096, 2), (1280, 9), (65536, 1), (1, 4096)])
 def test_decode_ragged_grids_wide(nb, ctx, gw, gh):
     """The wide kernel (hidden width 64, two hidden layers): grids whose width is
     not a multiple of its 256-texel tiles (per-texel features, ragged last tile),

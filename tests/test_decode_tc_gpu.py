@@ -115,7 +115,7 @@ def test_fp16_grid_long_strips(nb, ctx, gw, gh, levels):
     _check_fp16(got, emu, wl.material, _grid_x(wl.material, gw, gh))
 
 
-@pytest.mark.parametrize("gw,gh", [(200, 72), (130, 3), (7, 5), (128, 1), (256, 2)])
+@pytest.mark.parametrize("gw,gh", [(200, 72), (130, 3), (7, 5), (128, 1), (256, 2), (65536, 1), (1, 4096)])
 def test_fp16_ragged(nb, ctx, gw, gh):
     wl = synth.small_decode_workload(256, [12, 64, 64, 9], seed=310)
     got = _fp16_case(nb, ctx, wl, grid=(gw, gh))
