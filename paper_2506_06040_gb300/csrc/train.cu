@@ -2,6 +2,11 @@
 // (bilinear latent sampling + MLP 12-64-64-C), loss against the bilinearly
 // sampled target, backward through the MLP into every latent texel, Adam.
 //
+// k_gather (when the workspace has room): one thread per sample samples the
+// latents and the target and writes the sample's features and target channels
+// as one record, so the scattered taps of many samples are in flight at once;
+// k_train then reads the records coalesced (otherwise it samples them itself).
+//
 // k_train: persistent CTAs of 256 threads (one per SM) walk 256-sample tiles.
 // Per tile all activations live in shared memory, feature-major ([k][sample],
 // samples contiguous; backward deltas overwrite the activations they follow),
@@ -11,7 +16,7 @@
 // sums with Neumaier compensation (each thread owns fixed entries), written to
 // the workspace at the end; k_reduce_adam adds the CTA partials in a fixed
 // order (compensated), writes the gradients and applies Adam.  Latent
-// gradients: FP32 atomics (red.global.add).
+// gradients: FP32 atomics (16-byte vector adds with 4-float texels).
 #include <mutex>
 #include <string>
 
