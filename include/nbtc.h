@@ -49,7 +49,7 @@ typedef enum {
   NBTC_ERR_UNSUPPORTED = 2, /* valid request the library has no kernel for */
   NBTC_ERR_CUDA = 3,        /* a CUDA runtime call failed                    */
   NBTC_ERR_TIMEOUT = 4,     /* a device-side bounded wait expired            */
-  NBTC_ERR_BOUNDS = 5       /* a checked build caught an out-of-range index  */
+  NBTC_ERR_BOUNDS = 5       /* reserved (no build of this library reports it) */
 } nbtc_status;
 
 typedef enum {
