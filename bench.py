@@ -298,7 +298,7 @@ def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
     peak = _fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
     ctx.sync(stream)
     res = {"workload": wl.name, "steps_per_s": 1e3 / ms, "samples_per_s": wl.batch * 1e3 / ms, "ms_per_step": ms,
-           "kernels_per_step": 6, "layout": "latents [h][w][4], target [h][w][12] (padding channels unused)",
+           "kernels_per_step": 5, "layout": "latents [h][w][4], target [h][w][12] (padding channels unused)",
            "roofline": {"bound": "alu", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "frac": flop / (ms * 1e-3) / 1e12 / peak,
                         "note": "whole step (forward, backward, reduction, Adam) against the FP32 FFMA peak"}}
@@ -316,7 +316,7 @@ def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
     msq = statistics.mean(tq)
     ctx.sync(stream)
     res["qat"] = {"steps_per_s": 1e3 / msq, "samples_per_s": wl.batch * 1e3 / msq, "ms_per_step": msq,
-                  "kernels_per_step": 6 + 4 + 4 * 4}
+                  "kernels_per_step": 7}
     return res
 
 

@@ -71,9 +71,20 @@ nbtc_status train_step_qat(nbtc_context* ctx, const nbtc_train_args* A, const nb
                            cudaStream_t s);
 // Floats per latent texel of a training call (3 or 4), 0 when the stride is invalid.
 int latent_stride(const nbtc_train_args* A);
-// One Adam update (the step's betas, eps and step number; learning rate lr) of n parameters.
-nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, float* p, const float* g, float* m,
-                        float* v, int64_t n, cudaStream_t s);
+// One Adam update (the step's betas, eps and step number; learning rate lr) of
+// up to 12 parameter arrays of n[i] floats each, in one launch.
+struct AdamSeg {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  int64_t n;
+};
+struct AdamSegs {
+  AdamSeg seg[12];
+  int count;  // <= 12
+};
+nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, const AdamSegs& S, cudaStream_t s);
 nbtc_status launch_calibrate_fp32(nbtc_context* ctx, const DecodeArgs& a, const nbtc_mlp* mlp,
                                   int step, float* absmax, cudaStream_t s);
 

@@ -62,9 +62,21 @@ __device__ __forceinline__ float3 endpoint_value(const float* e, const QatThresh
                      (float)qlevel(e[2], T.t5, 31) / 31.f);
 }
 
+// Up to 4 levels per launch, level blockIdx.y: its raw parameters, its decoded
+// texture (or dL/dT) and the straight-through gradients.
+struct QatJobs {
+  QatLevelDev L[4];
+  float* tex[4];
+  float* g_e0[4];
+  float* g_e1[4];
+  float* g_alpha[4];
+};
+
 // One thread per texel: T = (1 - a) E0 + a E1, written with ls floats per texel
 // (3, or 4 with the padding channel set to 0).
-__global__ void k_qat_decode(QatLevelDev L, float* __restrict__ out, QatThresholds T, int ls) {
+__global__ void k_qat_decode(QatJobs J, QatThresholds T, int ls) {
+  const QatLevelDev L = J.L[blockIdx.y];
+  float* __restrict__ out = J.tex[blockIdx.y];
   const int64_t n = (int64_t)L.w * L.h;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int y = (int)(i / L.w), x = (int)(i - (int64_t)y * L.w);
@@ -84,8 +96,12 @@ __global__ void k_qat_decode(QatLevelDev L, float* __restrict__ out, QatThreshol
 
 // One thread per block: straight-through gradients of its two endpoints and
 // sixteen blend factors from dL/dT (ls floats per texel).
-__global__ void k_qat_backward(QatLevelDev L, const float* __restrict__ dT, float* __restrict__ g_e0,
-                               float* __restrict__ g_e1, float* __restrict__ g_alpha, QatThresholds T, int ls) {
+__global__ void k_qat_backward(QatJobs J, QatThresholds T, int ls) {
+  const QatLevelDev L = J.L[blockIdx.y];
+  const float* __restrict__ dT = J.tex[blockIdx.y];
+  float* __restrict__ g_e0 = J.g_e0[blockIdx.y];
+  float* __restrict__ g_e1 = J.g_e1[blockIdx.y];
+  float* __restrict__ g_alpha = J.g_alpha[blockIdx.y];
   const int wb = L.w >> 2;
   const int64_t nb = (int64_t)wb * (L.h >> 2);
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
@@ -173,7 +189,10 @@ nbtc_status qat_decode(nbtc_context* ctx, const nbtc_qat_level* q, float* out, c
   nbtc_status st = check_qat_level(q, false);
   if (st) return st;
   if (!out) return fail(NBTC_ERR_INVALID_ARG, "out NULL");
-  k_qat_decode<<<grid_for(ctx, (int64_t)q->width * q->height), 256, 0, s>>>(level_dev(q), out, make_thresholds(), 3);
+  QatJobs J{};
+  J.L[0] = level_dev(q);
+  J.tex[0] = out;
+  k_qat_decode<<<grid_for(ctx, (int64_t)q->width * q->height), 256, 0, s>>>(J, make_thresholds(), 3);
   return cuda_check(cudaGetLastError(), "launch k_qat_decode");
 }
 
@@ -201,23 +220,33 @@ nbtc_status train_step_qat(nbtc_context* ctx, const nbtc_train_args* A, const nb
       return fail(NBTC_ERR_INVALID_ARG, "QAT level size differs from the decoded latent size");
     if (!A->latents[k] || !A->latent_grads[k]) return fail(NBTC_ERR_INVALID_ARG, "latent or gradient NULL");
   }
+  // the four levels in one launch each: decode, straight-through backward, Adam
   const QatThresholds T = make_thresholds();
-  for (int k = 0; k < 4; ++k) {
-    k_qat_decode<<<grid_for(ctx, (int64_t)levels[k].width * levels[k].height), 256, 0, s>>>(
-        level_dev(&levels[k]), A->latents[k], T, ls);
-    if ((st = cuda_check(cudaGetLastError(), "launch k_qat_decode"))) return st;
-  }
-  if ((st = train_step_impl(ctx, A, loss, s, 3, nullptr, nullptr, A->workspace, A->workspace_bytes))) return st;
+  QatJobs D{}, B{};
+  AdamSegs S;
+  S.count = 12;
+  int64_t nt_max = 0, nb_max = 0;
   for (int k = 0; k < 4; ++k) {
     const nbtc_qat_level& q = levels[k];
     const int64_t nb = (int64_t)(q.width / 4) * (q.height / 4), nt = (int64_t)q.width * q.height;
-    k_qat_backward<<<grid_for(ctx, nb), 256, 0, s>>>(level_dev(&q), A->latent_grads[k], q.g_e0, q.g_e1, q.g_alpha, T, ls);
-    if ((st = cuda_check(cudaGetLastError(), "launch k_qat_backward"))) return st;
-    if ((st = launch_adam(ctx, A, A->lr_latent, q.e0, q.g_e0, q.m_e0, q.v_e0, 3 * nb, s))) return st;
-    if ((st = launch_adam(ctx, A, A->lr_latent, q.e1, q.g_e1, q.m_e1, q.v_e1, 3 * nb, s))) return st;
-    if ((st = launch_adam(ctx, A, A->lr_latent, q.alpha, q.g_alpha, q.m_alpha, q.v_alpha, nt, s))) return st;
+    nt_max = nt > nt_max ? nt : nt_max;
+    nb_max = nb > nb_max ? nb : nb_max;
+    D.L[k] = B.L[k] = level_dev(&q);
+    D.tex[k] = A->latents[k];
+    B.tex[k] = A->latent_grads[k];
+    B.g_e0[k] = q.g_e0;
+    B.g_e1[k] = q.g_e1;
+    B.g_alpha[k] = q.g_alpha;
+    S.seg[3 * k + 0] = AdamSeg{q.e0, q.g_e0, q.m_e0, q.v_e0, 3 * nb};
+    S.seg[3 * k + 1] = AdamSeg{q.e1, q.g_e1, q.m_e1, q.v_e1, 3 * nb};
+    S.seg[3 * k + 2] = AdamSeg{q.alpha, q.g_alpha, q.m_alpha, q.v_alpha, nt};
   }
-  return NBTC_OK;
+  k_qat_decode<<<dim3(grid_for(ctx, nt_max), 4), 256, 0, s>>>(D, T, ls);
+  if ((st = cuda_check(cudaGetLastError(), "launch k_qat_decode"))) return st;
+  if ((st = train_step_impl(ctx, A, loss, s, 3, nullptr, nullptr, A->workspace, A->workspace_bytes))) return st;
+  k_qat_backward<<<dim3(grid_for(ctx, nb_max), 4), 256, 0, s>>>(B, T, ls);
+  if ((st = cuda_check(cudaGetLastError(), "launch k_qat_backward"))) return st;
+  return launch_adam(ctx, A, A->lr_latent, S, s);
 }
 
 }  // namespace nbtc

@@ -664,15 +664,32 @@ __global__ void k_reduce_adam(const float* __restrict__ part, int nparts, int C,
   }
 }
 
-__global__ void k_adam_latent(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                              float* __restrict__ v, int64_t n, AdamHyper h) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float pp = p[i], mm = m[i], vv = v[i];
-    adam_update(pp, mm, vv, g[i], h);
-    p[i] = pp;
-    m[i] = mm;
-    v[i] = vv;
+// Adam over several parameter arrays in one launch: segment blockIdx.y.
+__global__ void k_adam_latent(AdamSegs S, AdamHyper h) {
+  const AdamSeg q = S.seg[blockIdx.y];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < q.n; i += (int64_t)gridDim.x * blockDim.x) {
+    float pp = q.p[i], mm = q.m[i], vv = q.v[i];
+    adam_update(pp, mm, vv, q.g[i], h);
+    q.p[i] = pp;
+    q.m[i] = mm;
+    q.v[i] = vv;
   }
+}
+
+// Zeroes up to 4 float arrays in one launch: array blockIdx.y.
+struct ZeroSeg {
+  float* p;
+  int64_t n;
+};
+struct ZeroSegs {
+  ZeroSeg seg[4];
+};
+__global__ void k_zero(ZeroSegs Z) {
+  const ZeroSeg z = Z.seg[blockIdx.y];
+  float* p = z.p;
+  const int64_t n = z.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0.f;
 }
 
 // ------------------------------------------------------------------ host
@@ -682,8 +699,7 @@ int latent_stride(const nbtc_train_args* A) {
   return ls == 3 || ls == 4 ? ls : 0;
 }
 
-nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, float* p, const float* g, float* m,
-                        float* v, int64_t n, cudaStream_t s) {
+nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, const AdamSegs& S, cudaStream_t s) {
   AdamHyper h;
   h.b1 = A->beta1;
   h.b2 = A->beta2;
@@ -691,10 +707,12 @@ nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, f
   h.bc1 = (float)(1.0 - pow((double)A->beta1, (double)A->step));
   h.bc2 = (float)(1.0 - pow((double)A->beta2, (double)A->step));
   h.lr = lr;
-  if (n <= 0) return NBTC_OK;
-  int grid = (int)((n + 255) / 256);
-  if (grid > ctx->sm_count * 16) grid = ctx->sm_count * 16;
-  k_adam_latent<<<grid, 256, 0, s>>>(p, g, m, v, n, h);
+  int64_t nmax = 0;
+  for (int i = 0; i < S.count; ++i) nmax = S.seg[i].n > nmax ? S.seg[i].n : nmax;
+  if (nmax <= 0) return NBTC_OK;
+  int64_t gx = (nmax + 255) / 256;
+  if (gx > ctx->sm_count * 16) gx = ctx->sm_count * 16;
+  k_adam_latent<<<dim3((unsigned)gx, (unsigned)S.count), 256, 0, s>>>(S, h);
   return cuda_check(cudaGetLastError(), "launch k_adam_latent");
 }
 
@@ -826,15 +844,17 @@ static nbtc_status launch_train_kernel(const nbtc_train_args* A, const TrainDev&
 }
 
 // Zeroes the latent gradients (this batch's gradient, not an accumulation).
-static nbtc_status zero_latent_grads(const nbtc_train_args* A, cudaStream_t s) {
+static nbtc_status zero_latent_grads(nbtc_context* ctx, const nbtc_train_args* A, cudaStream_t s) {
+  ZeroSegs Z;
+  int64_t nmax = 0;
   for (int k = 0; k < 4; ++k) {
-    nbtc_status st = cuda_check(
-        cudaMemsetAsync(A->latent_grads[k], 0, sizeof(float) * latent_stride(A) * (size_t)A->widths[k] * A->heights[k],
-                        s),
-        "memset latent grads");
-    if (st) return st;
+    Z.seg[k] = ZeroSeg{A->latent_grads[k], latent_stride(A) * (int64_t)A->widths[k] * A->heights[k]};
+    nmax = Z.seg[k].n > nmax ? Z.seg[k].n : nmax;
   }
-  return NBTC_OK;
+  int64_t gx = (nmax + 255) / 256;
+  if (gx > ctx->sm_count * 16) gx = ctx->sm_count * 16;
+  k_zero<<<dim3((unsigned)gx, 4u), 256, 0, s>>>(Z);
+  return cuda_check(cudaGetLastError(), "launch k_zero");
 }
 
 nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* loss, cudaStream_t s, int mode,
@@ -854,7 +874,7 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
   }
   if (!workspace || !aligned(workspace, 16) || workspace_bytes < (size_t)grid * kPart * sizeof(float))
     return fail(NBTC_ERR_INVALID_ARG, "workspace NULL, misaligned or too small");
-  if ((st = zero_latent_grads(A, s))) return st;
+  if ((st = zero_latent_grads(ctx, A, s))) return st;
   if ((st = pre_gather(ctx, A, d, grid, mode == kModeTrain, workspace, workspace_bytes, s))) return st;
   if (mode == kModeBwd) {
     if (!dy && A->batch > 0) return fail(NBTC_ERR_INVALID_ARG, "dy is NULL");
@@ -879,15 +899,13 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
                                                  A->grad_b, A->m_w, A->v_w, A->m_b, A->v_b, loss,
                                                  mode == kModeTrain ? 1 : 0, h);
   if ((st = cuda_check(cudaGetLastError(), "launch k_reduce_adam"))) return st;
-  if (latent_adam) {
-    h.lr = A->lr_latent;
-    for (int k = 0; k < 4; ++k) {
-      const int64_t n = latent_stride(A) * (int64_t)A->widths[k] * A->heights[k];
-      int g = (int)((n + 255) / 256);
-      if (g > ctx->sm_count * 16) g = ctx->sm_count * 16;
-      k_adam_latent<<<g, 256, 0, s>>>(A->latents[k], A->latent_grads[k], A->latent_m[k], A->latent_v[k], n, h);
-      if ((st = cuda_check(cudaGetLastError(), "launch k_adam_latent"))) return st;
-    }
+  if (latent_adam) {  // all four levels in one launch
+    AdamSegs S;
+    S.count = 4;
+    for (int k = 0; k < 4; ++k)
+      S.seg[k] = AdamSeg{A->latents[k], A->latent_grads[k], A->latent_m[k], A->latent_v[k],
+                         latent_stride(A) * (int64_t)A->widths[k] * A->heights[k]};
+    if ((st = launch_adam(ctx, A, A->lr_latent, S, s))) return st;
   }
   return NBTC_OK;
 }
