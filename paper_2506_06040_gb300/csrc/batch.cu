@@ -412,6 +412,7 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     if (M.latents.num_levels != 4) return fail(NBTC_ERR_UNSUPPORTED, "batched materials take 4 latent levels");
     LevelView lv[NBTC_MAX_LEVELS];
     if ((st = make_level_views(&M.latents, 0, lv))) return st;
+    if ((st = need_inputs(&M.latents, &M.mlp))) return st;
     size_t pb = 0;
     if ((st = tc_packed_bytes(&M.mlp, NBTC_FP16, &pb))) return st;
     const int h = M.mlp.num_layers - 1, c = M.mlp.dims[M.mlp.num_layers];
@@ -425,6 +426,7 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
       if (M.out_w <= 0 || M.out_h <= 0 || M.out_w % kTile) return fail(NBTC_ERR_INVALID_ARG, "out_w must be a positive multiple of 128");
       if ((int64_t)M.out_w * M.out_h / kTile >= (int64_t)1 << 31) return fail(NBTC_ERR_UNSUPPORTED, "material output too large");
       if (!aligned(M.out, 16)) return fail(NBTC_ERR_INVALID_ARG, "material out not 16-byte aligned");
+      if ((st = need_device(M.out, "material out"))) return st;  // written with bulk copies
       for (int k = 0; k < 4; ++k)
         if (M.latents.levels[k].width > M.out_w) return fail(NBTC_ERR_UNSUPPORTED, "latent level wider than the output");
     }
@@ -438,6 +440,10 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     if (frame->shaded && !aligned(frame->shaded, 16))
       return fail(NBTC_ERR_INVALID_ARG, "frame shaded output not 16-byte aligned");
     if (frame->shaded && nout < 8) return fail(NBTC_ERR_UNSUPPORTED, "the lighting pass needs at least 8 channels");
+    if ((st = need_readable(frame->mat_id, "frame mat_id")) || (st = need_readable(frame->uv, "frame uv")) ||
+        (st = need_readable(frame->lod, "frame lod")) || (frame->duv && (st = need_readable(frame->duv, "frame duv"))) ||
+        (st = need_device(frame->out, "frame out")) || (frame->shaded && (st = need_device(frame->shaded, "frame shaded"))))
+      return st;
     if ((int64_t)frame->width * frame->height >= (int64_t)1 << 31) return fail(NBTC_ERR_UNSUPPORTED, "frame too large");
   }
   nbtc_batch* B = new nbtc_batch();

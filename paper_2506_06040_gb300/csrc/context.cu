@@ -37,6 +37,40 @@ nbtc_status check_mlp(const nbtc_mlp* mlp) {
   return NBTC_OK;
 }
 
+PtrKind ptr_kind(const void* p) {
+  cudaPointerAttributes pa;
+  if (!p || cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+    cudaGetLastError();
+    return kPtrOther;
+  }
+  if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) return kPtrDevice;
+  if (pa.type == cudaMemoryTypeHost && pa.devicePointer) return kPtrPinned;
+  return kPtrOther;
+}
+
+nbtc_status need_readable(const void* p, const char* what) {
+  if (ptr_kind(p) == kPtrOther)
+    return fail(NBTC_ERR_INVALID_ARG, std::string(what) + " is neither device memory nor pinned host memory");
+  return NBTC_OK;
+}
+
+nbtc_status need_device(const void* p, const char* what) {
+  if (ptr_kind(p) != kPtrDevice) return fail(NBTC_ERR_INVALID_ARG, std::string(what) + " is not device memory");
+  return NBTC_OK;
+}
+
+nbtc_status need_inputs(const nbtc_latents* lat, const nbtc_mlp* mlp) {
+  nbtc_status st;
+  if (lat)
+    for (int k = 0; k < lat->num_levels && k < NBTC_MAX_LEVELS; ++k)
+      if ((st = need_readable(lat->levels[k].blocks, "a level's blocks"))) return st;
+  if (mlp) {
+    if ((st = need_readable(mlp->weights, "mlp weights"))) return st;
+    if ((st = need_readable(mlp->biases, "mlp biases"))) return st;
+  }
+  return NBTC_OK;
+}
+
 nbtc_status make_level_views(const nbtc_latents* lat, int mip, LevelView* views) {
   if (!lat) return fail(NBTC_ERR_INVALID_ARG, "latents is NULL");
   if (lat->num_levels < 1 || lat->num_levels > NBTC_MAX_LEVELS)
@@ -174,6 +208,7 @@ nbtc_status nbtc_bc1_decode_level(nbtc_context* ctx, const nbtc_level* level, in
   lat.levels[0] = *level;
   LevelView v;
   if ((st = make_level_views(&lat, mip, &v))) return st;
+  if ((st = need_inputs(&lat, nullptr)) || (st = need_readable(out_dev, "out"))) return st;
   return launch_bc1_decode(ctx, v, out_dev, (cudaStream_t)stream);
 }
 
@@ -190,6 +225,8 @@ static nbtc_status make_decode_args(nbtc_context* ctx, const nbtc_latents* lat, 
   if ((st = make_level_views(lat, 0, a.lv))) return st;
   if (n < 0) return fail(NBTC_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return NBTC_OK;  // nothing to decode; no pointer is touched
+  if ((st = need_inputs(lat, mlp))) return st;
+  if (uv && (st = need_readable(uv, "uv"))) return st;
   if (!uv) {
     if (grid_w <= 0 || grid_h <= 0 || (int64_t)grid_w * grid_h != n)
       return fail(NBTC_ERR_INVALID_ARG, "grid mode needs n == grid_w * grid_h > 0");
@@ -219,6 +256,7 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
   if (st) return st;
   if (step < 1) return fail(NBTC_ERR_INVALID_ARG, "step must be >= 1");
   if (!act_absmax_dev) return fail(NBTC_ERR_INVALID_ARG, "act_absmax is NULL");
+  if ((st = need_device(act_absmax_dev, "act_absmax"))) return st;
   DecodeArgs a;
   if ((st = make_decode_args(ctx, lat, mlp, nullptr, (int64_t)grid_w * grid_h, grid_w, grid_h, nullptr, a,
                              /*need_out=*/false)))
@@ -262,6 +300,7 @@ nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_m
       return launch_decode_fp32(ctx, a, mlp, (cudaStream_t)stream);
     case NBTC_FP16:
     case NBTC_FP8_E4M3:
+      if ((st = need_device(packed_dev, "packed MLP"))) return st;
       return launch_decode_tc(ctx, a, mlp, precision, packed_dev, (cudaStream_t)stream);
     default:
       return fail(NBTC_ERR_INVALID_ARG, "unknown precision");
@@ -287,6 +326,7 @@ nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const n
       return launch_decode_fp32(ctx, a, mlp, (cudaStream_t)stream);
     case NBTC_FP16:
     case NBTC_FP8_E4M3:
+      if ((st = need_device(packed_dev, "packed MLP"))) return st;
       return launch_decode_tc(ctx, a, mlp, precision, packed_dev, (cudaStream_t)stream);
     default:
       return fail(NBTC_ERR_INVALID_ARG, "unknown precision");
@@ -314,6 +354,9 @@ nbtc_status nbtc_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int32_t precis
   if ((st = check_mlp(mlp))) return st;
   if (precision != NBTC_FP16 && precision != NBTC_FP8_E4M3)
     return fail(NBTC_ERR_INVALID_ARG, "pack_mlp takes NBTC_FP16 or NBTC_FP8_E4M3");
+  // the packed image is later bulk-copied into shared memory: device memory only
+  if ((st = need_inputs(nullptr, mlp)) || (st = need_device(packed_dev, "packed MLP"))) return st;
+  if (act_absmax_dev && (st = need_readable(act_absmax_dev, "act_absmax"))) return st;
   return launch_pack_mlp(ctx, mlp, precision, act_absmax_dev, packed_dev, packed_bytes, (cudaStream_t)stream);
 }
 

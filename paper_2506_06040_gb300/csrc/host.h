@@ -71,6 +71,13 @@ nbtc_status train_step_qat(nbtc_context* ctx, const nbtc_train_args* A, const nb
                            cudaStream_t s);
 // Floats per latent texel of a training call (3 or 4), 0 when the stride is invalid.
 int latent_stride(const nbtc_train_args* A);
+// Pointer kinds the kernels can use: device (or managed) memory, or pinned host
+// memory reached over the host link (plain loads and stores only, no bulk copies).
+enum PtrKind { kPtrDevice, kPtrPinned, kPtrOther };
+PtrKind ptr_kind(const void* p);
+nbtc_status need_readable(const void* p, const char* what);  // device or pinned host
+nbtc_status need_device(const void* p, const char* what);    // device (or managed) only
+nbtc_status need_inputs(const nbtc_latents* lat, const nbtc_mlp* mlp);  // every level's blocks, weights, biases
 // One Adam update (the step's betas, eps and step number; learning rate lr) of
 // up to 12 parameter arrays of n[i] floats each, in one launch.
 struct AdamSeg {

@@ -253,3 +253,21 @@ def test_full_size_anisotropic_and_lit_frames(nb, ctx):
     bound = (256.0 + 16.0 * cond) * 2.0 ** -24 * np.abs(ref).max(axis=1) + 1e-6
     assert np.all(np.abs(lit[:, :3] - ref).max(axis=1) <= bound)
     plan.close()
+
+
+def test_plan_refuses_host_buffers(nb, ctx):
+    """Material outputs are written with bulk copies and frame buffers are read
+    and written by the kernels: host buffers are refused when the plan is made."""
+    from paper_2506_06040_gb300 import _abi
+    mats = [nb.Material.from_synth(synth.small_decode_workload(256, [12, 64, 64, 9], seed=70).material)]
+    with pytest.raises(nb.NbtcError) as e:
+        nb.Batch(ctx, mats, [(torch.empty((256 * 256, 9), dtype=torch.float16).pin_memory(), 256, 256)],
+                 autotune=False)
+    assert e.value.code == _abi.ERR_INVALID_ARG
+    h, w = 16, 128
+    fr = {"mat_id": torch.zeros((h, w), dtype=torch.int32), "uv": torch.zeros((h, w, 2), device="cuda"),
+          "lod": torch.zeros((h, w), device="cuda"), "out": torch.empty((h, w, 9), dtype=torch.float16, device="cuda")}
+    with pytest.raises(nb.NbtcError) as e:
+        nb.Batch(ctx, mats, None, fr, autotune=False)
+    assert e.value.code == _abi.ERR_INVALID_ARG
+    ctx.sync()

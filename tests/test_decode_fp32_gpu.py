@@ -180,6 +180,22 @@ def test_invalid_arguments(nb, ctx):
     with pytest.raises(nb.NbtcError) as e:
         nb.decode(ctx, mat, grid=(64, 64), out=torch.empty((100, 9), device="cuda")[1:])  # misaligned
     assert e.value.code == _abi.ERR_INVALID_ARG
+    # pointer kinds: pageable host memory is refused before any launch; pinned
+    # host uv is read over the host link; the packed image must be device memory
+    uv = synth.random_uv(3, 1000)
+    with pytest.raises(nb.NbtcError) as e:
+        nb.decode(ctx, mat, uv=torch.from_numpy(uv))
+    assert e.value.code == _abi.ERR_INVALID_ARG
+    want = nb.decode(ctx, mat, uv=torch.from_numpy(uv).cuda())
+    got = nb.decode(ctx, mat, uv=torch.from_numpy(uv).pin_memory())
+    ctx.sync()
+    assert torch.equal(got, want)
+    wl64 = synth.small_decode_workload(256, [12, 64, 64, 9], seed=12)
+    mat64 = nb.Material.from_synth(wl64.material)
+    packed = nb.pack_mlp(ctx, mat64, nb.FP16)
+    with pytest.raises(nb.NbtcError) as e:
+        nb.decode(ctx, mat64, nb.FP16, packed.cpu(), grid=(256, 16))
+    assert e.value.code == _abi.ERR_INVALID_ARG
     mat.level_meta[0] = (66, 64, 1, 0.0)  # not a multiple of 4
     with pytest.raises(nb.NbtcError) as e:
         nb.decode(ctx, mat, grid=(8, 8))
