@@ -178,6 +178,10 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
  *  - precision NBTC_FP32: `packed_dev` NULL, `out_dev` n x N FP32.
  *    NBTC_FP16 / NBTC_FP8_E4M3: `packed_dev` from nbtc_pack_mlp() with the
  *    same precision, `out_dev` n x N FP16.  out_dev 16-byte aligned.
+ *  - Inputs (level blocks, MLP weights and biases, uv_dev) are device memory or
+ *    pinned host memory (read over the host link); packed_dev is device memory
+ *    (it is bulk-copied into shared memory); anything else is
+ *    NBTC_ERR_INVALID_ARG, checked before any launch.
  *  - out_dev is device memory or, for NBTC_FP32 only, pinned host memory
  *    (cudaHostAlloc / cudaHostRegister): the kernel then stores the texels
  *    straight into host memory over the host link, with no staging buffer or
@@ -397,7 +401,10 @@ typedef struct {
 /* Builds a plan (allocates its device buffers, packs the MLPs in FP16, builds
  * the work lists, autotunes if asked, captures the graphs).  `mats` is a host
  * array of `count` materials (<= 1024); `frame` may be NULL.  Device pointers in
- * `mats` and `frame` must stay valid while the plan is used. */
+ * `mats` and `frame` must stay valid while the plan is used.  Material outputs
+ * and the frame's out / shaded buffers must be device memory; the materials'
+ * inputs and the frame's mat_id / uv / lod / duv device or pinned host memory
+ * (NBTC_ERR_INVALID_ARG otherwise, checked here). */
 nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats, int32_t count,
                               const nbtc_frame* frame, int32_t flags, nbtc_batch** plan, void* stream);
 
