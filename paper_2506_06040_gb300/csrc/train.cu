@@ -745,6 +745,23 @@ static nbtc_status check_train(const nbtc_train_args* A, bool need_target, bool 
   if (A->batch < 0) return fail(NBTC_ERR_INVALID_ARG, "batch < 0");
   if (A->batch > 0 && (!A->uv || !aligned(A->uv, 8))) return fail(NBTC_ERR_INVALID_ARG, "uv NULL or not 8-byte aligned");
   if (A->loss != NBTC_LOSS_MSE && A->loss != NBTC_LOSS_L1) return fail(NBTC_ERR_INVALID_ARG, "unknown loss");
+  // pointer kinds: every buffer the kernels touch is device memory or pinned host memory
+  nbtc_status pk;
+  for (int k = 0; k < 4; ++k) {
+    if ((pk = need_readable(A->latents[k], "latents")) || (pk = need_readable(A->latent_grads[k], "latent_grads")))
+      return pk;
+    if (need_latent_adam &&
+        ((pk = need_readable(A->latent_m[k], "latent_m")) || (pk = need_readable(A->latent_v[k], "latent_v"))))
+      return pk;
+  }
+  if ((pk = need_readable(m.weights, "mlp weights")) || (pk = need_readable(m.biases, "mlp biases")) ||
+      (pk = need_readable(A->grad_w, "grad_w")) || (pk = need_readable(A->grad_b, "grad_b")))
+    return pk;
+  if (need_adam && ((pk = need_readable(A->m_w, "m_w")) || (pk = need_readable(A->v_w, "v_w")) ||
+                    (pk = need_readable(A->m_b, "m_b")) || (pk = need_readable(A->v_b, "v_b"))))
+    return pk;
+  if (need_target && (pk = need_readable(A->target, "target"))) return pk;
+  if (A->batch > 0 && (pk = need_readable(A->uv, "uv"))) return pk;
   return NBTC_OK;
 }
 

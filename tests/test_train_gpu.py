@@ -203,6 +203,11 @@ def test_invalid_strides(nb, ctx):
     assert run(lambda a: a.latents.__setitem__(1, a.latents[1] + 4)) == _abi.ERR_INVALID_ARG
     with pytest.raises(ValueError):
         model.train_step(ctx, uv, tgt[..., :8].contiguous())
+    # a pageable host target or uv is refused before any launch
+    tgt_host = tgt.cpu()
+    assert run(lambda a: setattr(a, "target", tgt_host.data_ptr())) == _abi.ERR_INVALID_ARG
+    uv_host = uv.cpu()
+    assert run(lambda a: setattr(a, "uv", uv_host.data_ptr())) == _abi.ERR_INVALID_ARG
     ctx.sync()
 
 
