@@ -226,6 +226,9 @@ nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const n
  * the target 16 bytes at a time; its padding channels are never used.  Loss: mean over batch and
  * channels of (y - t)^2 (NBTC_LOSS_MSE) or |y - t| (NBTC_LOSS_L1).
  *
+ * Every array is device memory or pinned host memory (pageable host memory is
+ * NBTC_ERR_INVALID_ARG, checked before any launch).
+ *
  * Gradient sums over the batch use compensated (Neumaier) FP32 summation;
  * latent gradients are accumulated with FP32 atomics (their summation order
  * varies between runs).  Adam follows the PyTorch form with bias correction:
