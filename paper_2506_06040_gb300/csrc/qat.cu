@@ -172,6 +172,13 @@ nbtc_status check_qat_level(const nbtc_qat_level* q, bool step) {
   if (step && (!q->g_e0 || !q->g_e1 || !q->g_alpha || !q->m_e0 || !q->v_e0 || !q->m_e1 || !q->v_e1 ||
                !q->m_alpha || !q->v_alpha))
     return fail(NBTC_ERR_INVALID_ARG, "QAT gradients or moments NULL");
+  // pointer kinds: device or pinned host memory
+  const void* ptrs[12] = {q->e0, q->e1, q->alpha, q->g_e0, q->g_e1, q->g_alpha,
+                          q->m_e0, q->v_e0, q->m_e1, q->v_e1, q->m_alpha, q->v_alpha};
+  for (int i = 0; i < (step ? 12 : 3); ++i) {
+    nbtc_status st = need_readable(ptrs[i], "a QAT parameter, gradient or moment array");
+    if (st) return st;
+  }
   return NBTC_OK;
 }
 
@@ -189,6 +196,7 @@ nbtc_status qat_decode(nbtc_context* ctx, const nbtc_qat_level* q, float* out, c
   nbtc_status st = check_qat_level(q, false);
   if (st) return st;
   if (!out) return fail(NBTC_ERR_INVALID_ARG, "out NULL");
+  if ((st = need_readable(out, "out"))) return st;
   QatJobs J{};
   J.L[0] = level_dev(q);
   J.tex[0] = out;
@@ -200,6 +208,7 @@ nbtc_status qat_encode(nbtc_context* ctx, const nbtc_qat_level* q, uint64_t* blo
   nbtc_status st = check_qat_level(q, false);
   if (st) return st;
   if (!blocks || !aligned(blocks, 8)) return fail(NBTC_ERR_INVALID_ARG, "blocks NULL or not 8-byte aligned");
+  if ((st = need_readable(blocks, "blocks"))) return st;
   k_qat_encode<<<grid_for(ctx, (int64_t)(q->width / 4) * (q->height / 4)), 256, 0, s>>>(level_dev(q), blocks,
                                                                                       make_thresholds());
   return cuda_check(cudaGetLastError(), "launch k_qat_encode");
