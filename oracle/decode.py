@@ -1,7 +1,8 @@
 """Whole decode of a material at given uv or on its texel-centre grid (Sec. 3.1):
 BC1 decode of every latent level, bilinear sampling with the per-level shift,
-concatenation, MLP.  Precision "fp64" is the plain definition; "fp16" and
-"fp8" are the quantisation emulator of the precision forms."""
+concatenation, MLP.  Precision "fp64" is the plain definition; "fp16", "fp8"
+and the split-operand "fp16s", "fp8s" are the quantisation emulator of the
+precision forms."""
 from __future__ import annotations
 
 import numpy as np
@@ -30,7 +31,19 @@ def run_mlp(material, x, precision: str = "fp64", fp8=None):
     if precision == "fp8":
         sw, sa = fp8
         return emulate.forward_fp8(x, m.weights, m.biases, sw, sa)
+    if precision == "fp16s":
+        return emulate.forward_fp16_split(x, m.weights, m.biases)
+    if precision == "fp8s":
+        sw, sa = fp8
+        return emulate.forward_fp8_split(x, m.weights, m.biases, sw, sa)
     raise ValueError(precision)
+
+
+def mlp_interval(material, x, precision: str, fp8=None, **error_model):
+    """(y, y_min, y_max) of a precision form: emulated FP16 output and the outputs
+    admissible under the FP32 error model of `emulate.output_interval`."""
+    m = material.mlp
+    return emulate.output_interval(precision, x, m.weights, m.biases, fp8, **error_model)
 
 
 def decode_uv(material, uv: np.ndarray, precision: str = "fp64", fp8=None, tex=None) -> np.ndarray:
