@@ -52,11 +52,22 @@ typedef enum {
   NBTC_ERR_BOUNDS = 5       /* reserved (no build of this library reports it) */
 } nbtc_status;
 
+/* Precision forms of the decode (Sec. 4 runs the MLP on matrix units in low
+ * precision).  The split forms carry every weight and activation as a pair
+ * hi + lo of the narrow format (FP16: hi = RN16(v), lo = RN16(v - hi); E4M3:
+ * v16 = RN16(v / scale), hi = E4M3(v16), lo = E4M3(v16 - hi)) and sum the three
+ * products hi(A) hi(W) + lo(A) hi(W) + hi(A) lo(W) per layer in one FP32
+ * accumulator: every multiply still reads the narrow format, at three times
+ * the tensor work, and the result keeps most of the precision the single
+ * rounding loses (max abs error vs FP64 on a He-initialised 12-64-64-64-9
+ * decode: FP16 3.2e-3 -> 9.8e-4, the FP16 output rounding; E4M3 0.37 -> 1.2e-2). */
 typedef enum {
-  NBTC_FP32 = 0,     /* FP32 SIMT arithmetic (FFMA), FP32 output              */
-  NBTC_FP16 = 1,     /* FP16 operands on tcgen05, FP32 accumulate, FP16 output */
-  NBTC_FP8_E4M3 = 2  /* E4M3 operands on tcgen05 with per-layer power-of-two
-                        scales, FP32 accumulate, FP16 output                   */
+  NBTC_FP32 = 0,            /* FP32 SIMT arithmetic (FFMA), FP32 output              */
+  NBTC_FP16 = 1,            /* FP16 operands on tcgen05, FP32 accumulate, FP16 output */
+  NBTC_FP8_E4M3 = 2,        /* E4M3 operands on tcgen05 with per-layer power-of-two
+                               scales, FP32 accumulate, FP16 output                   */
+  NBTC_FP16_SPLIT = 3,      /* split FP16 operands, otherwise as NBTC_FP16            */
+  NBTC_FP8_E4M3_SPLIT = 4   /* split E4M3 operands, otherwise as NBTC_FP8_E4M3        */
 } nbtc_precision;
 
 typedef enum { NBTC_CLAMP = 0, NBTC_WRAP = 1 } nbtc_address;
@@ -107,7 +118,9 @@ typedef struct nbtc_context nbtc_context;
  * device is not compute capability 10.3, NBTC_ERR_CUDA when CUDA fails.
  * Two environment variables, read here, select kernel shapes for measurement
  * (results are identical either way): NBTC_TC_GROUPS=3 runs the single-material
- * tensor-core decode with 3 warpgroups per CTA instead of 4, NBTC_FP32_GROUPS=1
+ * tensor-core decode with 3 warpgroups per CTA instead of 4 (NBTC_TC_GROUPS=2
+ * runs the split FP16 form as 2 warpgroups of two tile slots instead of 4 of
+ * one), NBTC_FP32_GROUPS=1
  * runs the FP32 wide decode as one 512-thread group per CTA instead of two
  * independent 256-thread groups. */
 nbtc_status nbtc_create(int device, nbtc_context** ctx);
@@ -151,9 +164,10 @@ nbtc_status nbtc_bc1_decode_level(nbtc_context* ctx, const nbtc_level* level, in
 nbtc_status nbtc_packed_mlp_bytes(const nbtc_mlp* mlp, int32_t precision, size_t* bytes);
 
 /* Lays the MLP out for the tensor-core forms: weights converted to FP16 or
- * E4M3 (round to nearest even, E4M3 saturating) in the shared-memory image the
- * decode kernel copies in one bulk transfer, plus FP32 biases and scales.
- * For NBTC_FP8_E4M3 `act_absmax_dev` must hold, per layer, the largest
+ * E4M3 (round to nearest even, E4M3 saturating; the split forms store hi and
+ * lo) in the shared-memory image the decode kernel copies in one bulk
+ * transfer, plus FP32 biases and scales.
+ * For NBTC_FP8_E4M3 and NBTC_FP8_E4M3_SPLIT `act_absmax_dev` must hold, per layer, the largest
  * magnitude of that layer's input over a calibration set (nbtc_fp8_calibrate);
  * the layer scales are then sw_l = pow2ceil(absmax(W_l) / 448) and
  * sa_l = pow2ceil(act_absmax_l / 448).  `packed_dev` must be 16-byte aligned
@@ -176,8 +190,9 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
  *    u = (i + 0.5) / grid_w, v = (j + 0.5) / grid_h, row-major.
  *  - uv_dev != NULL: n (u, v) FP32 pairs, interleaved; grid_w, grid_h ignored.
  *  - precision NBTC_FP32: `packed_dev` NULL, `out_dev` n x N FP32.
- *    NBTC_FP16 / NBTC_FP8_E4M3: `packed_dev` from nbtc_pack_mlp() with the
- *    same precision, `out_dev` n x N FP16.  out_dev 16-byte aligned.
+ *    NBTC_FP16 / NBTC_FP8_E4M3 / NBTC_FP16_SPLIT / NBTC_FP8_E4M3_SPLIT:
+ *    `packed_dev` from nbtc_pack_mlp() with the same precision, `out_dev`
+ *    n x N FP16.  out_dev 16-byte aligned.
  *  - Inputs (level blocks, MLP weights and biases, uv_dev) are device memory or
  *    pinned host memory (read over the host link); packed_dev is device memory
  *    (it is bulk-copied into shared memory); anything else is
@@ -185,8 +200,8 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
  *  - out_dev is device memory or, for NBTC_FP32 only, pinned host memory
  *    (cudaHostAlloc / cudaHostRegister): the kernel then stores the texels
  *    straight into host memory over the host link, with no staging buffer or
- *    copy; completion is the stream's.  Pinned host output with NBTC_FP16 /
- *    NBTC_FP8_E4M3 is NBTC_ERR_UNSUPPORTED (their kernels store with bulk
+ *    copy; completion is the stream's.  Pinned host output with a tensor-core
+ *    precision is NBTC_ERR_UNSUPPORTED (their kernels store with bulk
  *    copies, kept to device memory); any other pointer (pageable host memory)
  *    is NBTC_ERR_INVALID_ARG.
  * Shapes with a kernel: 4 latent levels, hidden width 16, 32 or 64 (all

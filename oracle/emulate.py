@@ -142,7 +142,8 @@ def forward_fp8_split(x: np.ndarray, weights: list, biases: list, sw: list, sa: 
 #  - FP32 noise: the kernel's feature deviates from the exact one by noise of
 #    standard deviation sigma_x; an FP32 sum of n exact products and a bias by
 #    noise of standard deviation 2^-24 sqrt(n) sqrt(sum of squared terms)
-#    (independent roundings of at most half an FP32 unit of the partial sums);
+#    (independent roundings of at most half an FP32 unit of the partial sums;
+#    times acc_scale for a tensor-core kind whose accumulator is coarser);
 #    noise passes a near-identity operand representation (the FP16 split, whose
 #    own lo rounding adds as noise too) and adds in quadrature through a dot
 #    product.  A value is in doubt within k standard deviations.
@@ -185,12 +186,16 @@ def _change(f, v, p):
 
 
 def output_interval(form: str, x: np.ndarray, weights: list, biases: list, scales=None,
-                    sigma_x: float = 2.0 ** -24, k: float = 6.0):
+                    sigma_x: float = 2.0 ** -24, k: float = 6.0, acc_scale=None):
     """(y, y_min, y_max): the emulated FP16 output of `form` and the interval of
     FP16 outputs admissible for a kernel under the error model above.
-    scales = (sw, sa) for the FP8 forms."""
+    scales = (sw, sa) for the FP8 forms; acc_scale = accumulation noise in units
+    of FP32 round-to-nearest (default: 1 for the FP16 forms, 4 for the E4M3 forms,
+    whose tensor-core accumulation measures about two bits coarser)."""
     assert form in FORMS
     fp8 = form in ("fp8", "fp8s")
+    if acc_scale is None:
+        acc_scale = 4.0 if fp8 else 1.0
     split = form in ("fp16s", "fp8s")
     dense = form == "fp16s"            # representation ~ identity: noise passes through
     n = len(weights)
@@ -223,7 +228,7 @@ def output_interval(form: str, x: np.ndarray, weights: list, biases: list, scale
         z = (ah @ wh.T + al @ wh.T + ah @ wl.T + bh + bl) * s + bias
         sq = (ah ** 2 @ (wh ** 2).T + al ** 2 @ (wh ** 2).T + ah ** 2 @ (wl ** 2).T + bh ** 2 + bl ** 2) * s * s
         nterms = (3 if split else 1) * w.shape[1] + (0 if fp8 else (2 if split else 1))
-        sig_z = np.sqrt(carried_sig ** 2 @ ((wh + wl) ** 2).T * s * s + nterms * 2.0 ** -48 * sq)
+        sig_z = np.sqrt(carried_sig ** 2 @ ((wh + wl) ** 2).T * s * s + nterms * (acc_scale * 2.0 ** -24) ** 2 * sq)
         if fp8:   # the FP32 scale-and-bias FMA of the epilogue
             sig_z = np.sqrt(sig_z ** 2 + (2.0 ** -24 * (np.abs(z) + np.abs(b))) ** 2)
         jmp_z = (carried_jmp @ np.abs(wh + wl).T + dhi @ np.abs(wl).T) * s

@@ -104,8 +104,8 @@ def _bilinear_bc1(level_blocks, w, h, u, v, shift, address):
             + (1 - fx) * fy * t(xa, yb) + fx * fy * t(xb, yb))
 
 
-def decode_pixels_direct(material, uv: np.ndarray, lod: np.ndarray, precision: str = "fp16") -> np.ndarray:
-    """decode_pixels without decoding whole mips: each tap's BC1 texel is
+def pixel_features_direct(material, uv: np.ndarray, lod: np.ndarray) -> np.ndarray:
+    """[n, 12] trilinear features of the given pixels, each tap's BC1 texel
     decoded on demand (for spot checks of large frames)."""
     u, v = uv[:, 0].astype(np.float64), uv[:, 1].astype(np.float64)
     feats = []
@@ -126,7 +126,12 @@ def decode_pixels_direct(material, uv: np.ndarray, lod: np.ndarray, precision: s
                 acc[sel] += wt * smp
             w, h = max(4, w // 2), max(4, h // 2)
         feats.append(acc)
-    x = np.concatenate(feats, axis=-1)
+    return np.concatenate(feats, axis=-1)
+
+
+def decode_pixels_direct(material, uv: np.ndarray, lod: np.ndarray, precision: str = "fp16") -> np.ndarray:
+    """decode_pixels without decoding whole mips (see pixel_features_direct)."""
+    x = pixel_features_direct(material, uv, lod)
     mlp = material.mlp
     if precision == "fp16":
         return emulate.forward_fp16(x, mlp.weights, mlp.biases)
@@ -161,7 +166,11 @@ def aniso_features(material, levels_mips_rgb: list, uv: np.ndarray, duv: np.ndar
                    max_aniso: int) -> np.ndarray:
     """[n, 12] features: the mean of N trilinear probes at uv + (i / (N + 1) - 1/2)
     times the major-axis derivative, i = 1..N, each level at lod
-    bias + log2(Pmax W_k / N) (FP64 apart from the decision of N)."""
+    bias + log2(Pmax W_k / N).  FP64 apart from the decision of N and the probe
+    coordinates: a probe samples the latents at a texture coordinate, which is
+    an FP32 value (Sec. 3.1 samples T_k at the FP32 uv a shader passes), formed
+    as RN32(u + o d) with the offset o = RN32(RN32(i / (N + 1)) - 1/2) -- one
+    rounding of the exact product and sum, as an FMA takes it."""
     n, along_x, pmax = aniso_count(duv, max_aniso)
     d = np.asarray(duv, dtype=np.float64)
     au = np.where(along_x, d[:, 0], d[:, 2])
@@ -173,8 +182,12 @@ def aniso_features(material, levels_mips_rgb: list, uv: np.ndarray, duv: np.ndar
     feats = np.zeros((len(u), 12))
     for i in range(1, int(n.max()) + 1):
         sel = n >= i
-        off = i / (n[sel] + 1.0) - 0.5
-        uu, vv = u[sel] + off * au[sel], v[sel] + off * av[sel]
+        off = ((np.float32(i) / (n[sel] + 1).astype(np.float32)) - np.float32(0.5)).astype(np.float64)
+        # off * a is exact in FP64 (two 24-bit significands); the sum is rounded
+        # once more in FP64 before the FP32 rounding, which changes the FP32 result
+        # only when the FP64 sum lands exactly on an FP32 midpoint
+        uu = (u[sel] + off * au[sel]).astype(np.float32).astype(np.float64)
+        vv = (v[sel] + off * av[sel]).astype(np.float32).astype(np.float64)
         for k, (lv, mips) in enumerate(zip(material.levels, levels_mips_rgb)):
             lam = base[sel] + np.log2(float(lv.width))
             feats[sel, 3 * k:3 * k + 3] += trilinear(mips, uu, vv, lam, lv.shift, material.address)

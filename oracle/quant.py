@@ -20,16 +20,12 @@ import numpy as np
 
 
 def _round_to_quantum(x: np.ndarray, min_exp: int, frac_bits: int) -> np.ndarray:
+    """Nearest multiple (ties to even) of the quantum 2^(e - frac_bits) of x's
+    binade 2^e <= |x| < 2^(e+1), with e clamped below at min_exp (subnormals)."""
     x = np.asarray(x, dtype=np.float64)
-    ax = np.abs(x)
-    with np.errstate(divide="ignore"):
-        e = np.floor(np.log2(np.where(ax > 0, ax, 1.0)))
-    # np.log2 may be off by one next to a power of two: fix e so 2^e <= |x| < 2^(e+1)
-    e = np.where(np.ldexp(1.0, e.astype(np.int64)) > ax, e - 1, e)
-    e = np.where(np.ldexp(1.0, (e + 1).astype(np.int64)) <= ax, e + 1, e)
-    e = np.maximum(e, min_exp)
-    q = np.ldexp(1.0, (e - frac_bits).astype(np.int64))
-    return np.where(ax > 0, np.rint(x / q) * q, x)
+    _, e = np.frexp(x)  # x = m 2^e with 1/2 <= |m| < 1: the binade exponent is e - 1 (exact)
+    q = np.ldexp(1.0, np.maximum(e - 1, min_exp) - frac_bits)
+    return np.rint(x / q) * q  # x / q and the product are exact (powers of two); rint ties to even
 
 
 def round_fp16(x) -> np.ndarray:

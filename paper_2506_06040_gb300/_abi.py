@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libnbtc.so")
 
 MAX_LEVELS, MAX_LAYERS, MAX_MIPS = 8, 4, 16
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_BOUNDS = range(6)
-FP32, FP16, FP8_E4M3 = 0, 1, 2
+FP32, FP16, FP8_E4M3, FP16_SPLIT, FP8_E4M3_SPLIT = 0, 1, 2, 3, 4
 CLAMP, WRAP = 0, 1
 LOSS_MSE, LOSS_L1 = 0, 1
 

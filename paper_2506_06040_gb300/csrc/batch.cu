@@ -241,7 +241,7 @@ static nbtc_status enqueue_decode(nbtc_context* ctx, nbtc_batch* B, cudaStream_t
   p.chunks = B->dchunks;
   p.nchunks_dev = B->dnchunks;
   p.chunk_counter = B->dcounter;
-  return launch_tc_args(ctx, p, B->nhid, false, B->W, ctx->sm_count, s);
+  return launch_tc_args(ctx, p, B->nhid, kF16, B->W, 2, ctx->sm_count, s);
 }
 
 // Lighting constants of a frame: unit directions and the half vector, in double
@@ -307,7 +307,7 @@ static nbtc_status enqueue_render(nbtc_context* ctx, nbtc_batch* B, cudaStream_t
   p.tile_w = F.tw;
   p.tile_h = F.th;
   p.tiles_x = F.tiles_x;
-  return launch_tc_args(ctx, p, B->nhid, false, B->Wf, ctx->sm_count, s);
+  return launch_tc_args(ctx, p, B->nhid, kF16, B->Wf, 2, ctx->sm_count, s);
 }
 
 static nbtc_status set_tile_shape(nbtc_batch* B, int tw, int th) {

@@ -134,7 +134,7 @@ nbtc_status nbtc_create(int device, nbtc_context** out) {
   nbtc_context* ctx = new nbtc_context();
   ctx->device = device;
   ctx->sm_count = prop.multiProcessorCount;
-  if (const char* e = getenv("NBTC_TC_GROUPS")) ctx->tc_groups = atoi(e) == 3 ? 3 : 4;
+  if (const char* e = getenv("NBTC_TC_GROUPS")) ctx->tc_groups = atoi(e) == 3 ? 3 : atoi(e) == 2 ? 2 : 4;
   if (const char* e = getenv("NBTC_FP32_GROUPS")) ctx->fp32_groups = atoi(e) == 1 ? 1 : 2;
   if ((st = cuda_check(cudaMalloc(&ctx->status_dev, sizeof(int)), "cudaMalloc(status)"))) {
     delete ctx;
@@ -300,6 +300,8 @@ nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_m
       return launch_decode_fp32(ctx, a, mlp, (cudaStream_t)stream);
     case NBTC_FP16:
     case NBTC_FP8_E4M3:
+    case NBTC_FP16_SPLIT:
+    case NBTC_FP8_E4M3_SPLIT:
       if ((st = need_device(packed_dev, "packed MLP"))) return st;
       return launch_decode_tc(ctx, a, mlp, precision, packed_dev, (cudaStream_t)stream);
     default:
@@ -326,6 +328,8 @@ nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const n
       return launch_decode_fp32(ctx, a, mlp, (cudaStream_t)stream);
     case NBTC_FP16:
     case NBTC_FP8_E4M3:
+    case NBTC_FP16_SPLIT:
+    case NBTC_FP8_E4M3_SPLIT:
       if ((st = need_device(packed_dev, "packed MLP"))) return st;
       return launch_decode_tc(ctx, a, mlp, precision, packed_dev, (cudaStream_t)stream);
     default:
@@ -341,7 +345,7 @@ nbtc_status nbtc_packed_mlp_bytes(const nbtc_mlp* mlp, int32_t precision, size_t
     *bytes = 0;
     return NBTC_OK;
   }
-  if (precision != NBTC_FP16 && precision != NBTC_FP8_E4M3) return fail(NBTC_ERR_INVALID_ARG, "unknown precision");
+  if (precision < NBTC_FP16 || precision > NBTC_FP8_E4M3_SPLIT) return fail(NBTC_ERR_INVALID_ARG, "unknown precision");
   return tc_packed_bytes(mlp, precision, bytes);
 }
 
@@ -352,8 +356,8 @@ nbtc_status nbtc_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int32_t precis
   nbtc_status st = enter(ctx);
   if (st) return st;
   if ((st = check_mlp(mlp))) return st;
-  if (precision != NBTC_FP16 && precision != NBTC_FP8_E4M3)
-    return fail(NBTC_ERR_INVALID_ARG, "pack_mlp takes NBTC_FP16 or NBTC_FP8_E4M3");
+  if (precision < NBTC_FP16 || precision > NBTC_FP8_E4M3_SPLIT)
+    return fail(NBTC_ERR_INVALID_ARG, "pack_mlp takes a tensor-core precision (FP16, E4M3 or their split forms)");
   // the packed image is later bulk-copied into shared memory: device memory only
   if ((st = need_inputs(nullptr, mlp)) || (st = need_device(packed_dev, "packed MLP"))) return st;
   if (act_absmax_dev && (st = need_readable(act_absmax_dev, "act_absmax"))) return st;

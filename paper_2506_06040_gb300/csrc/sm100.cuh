@@ -210,6 +210,45 @@ __device__ __forceinline__ uint16_t cvt_e4m3x2(float lo, float hi) {
   return d;
 }
 
+// {lo, hi} e4m3x2 <- f16x2 (saturating, round to nearest even), and back (exact)
+__device__ __forceinline__ uint16_t cvt_e4m3x2_f16x2(uint32_t v) {
+  uint16_t d;
+  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(d) : "r"(v));
+  return d;
+}
+__device__ __forceinline__ uint32_t cvt_f16x2_e4m3x2(uint16_t v) {
+  uint32_t d;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(d) : "h"(v));
+  return d;
+}
+__device__ __forceinline__ float2 f16x2_to_float2(uint32_t v) {
+  float2 r;
+  asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n cvt.f32.f16 %0, l;\n cvt.f32.f16 %1, h;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "r"(v));
+  return r;
+}
+
+// Split operands: a value as hi + lo of the narrow format.
+//  FP16:  hi = RN16(v), lo = RN16(v - hi) (v - hi is exact in FP32)
+__device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  hi = cvt_f16x2(a, b);
+  const float2 h = f16x2_to_float2(hi);
+  lo = cvt_f16x2(a - h.x, b - h.y);
+}
+__device__ __forceinline__ void split_relu_f16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  split_f16x2(fmaxf(a, 0.f), fmaxf(b, 0.f), hi, lo);
+}
+//  E4M3 (of an FP16 pair v16): hi = E4M3(v16), lo = E4M3(v16 - hi); the
+//  residual of rounding an FP16 value to E4M3 is itself an FP16 value, so the
+//  FP16 subtraction is exact
+__device__ __forceinline__ void split_e4m3x2(uint32_t v16, uint16_t& hi, uint16_t& lo) {
+  hi = cvt_e4m3x2_f16x2(v16);
+  uint32_t res;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(res) : "r"(v16), "r"(cvt_f16x2_e4m3x2(hi)));
+  lo = cvt_e4m3x2_f16x2(res);
+}
+
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }

@@ -13,21 +13,42 @@ constexpr int kHid = 64;             // hidden width of the tensor-core forms
 constexpr int kOutPad = 16;          // output layer N (channels padded)
 constexpr int kMaxOut = 16;
 
+// Operand forms of the tensor-core decode.  The split forms carry every weight
+// and activation as a pair hi + lo of the narrow format and run three products
+// per layer into one FP32 accumulator: hi(A) hi(W) + lo(A) hi(W) + hi(A) lo(W).
+enum TcForm { kF16 = 0, kF8 = 1, kF16Split = 2, kF8Split = 3 };
+
 // Byte layout of a packed MLP (identical in global memory and shared memory).
-// FP16: every layer's bias enters the MMA as an FP16 operand -- layer 1 through
-// K column 12 of W1 (A0 carries a 1 there), later layers through a small
-// [N x 16] bias tile multiplied by a tile of ones.  FP8: the FP32 bias and the
-// per-layer scale are applied in the epilogue.
+// FP16 forms: every layer's bias enters the MMA as FP16 operand(s) -- layer 1
+// through a K column of W1 (A0 carries a 1 there), later layers through a
+// small [N x 16] bias tile multiplied by a tile of ones (split: column 0 holds
+// hi(b), column 1 lo(b)).  FP8 forms: the FP32 bias and the per-layer scale are
+// applied in the epilogue.  Split forms store every weight tile twice, hi then lo.
+//
+// W1 (layer 1, K-major, no swizzle) rows:
+//   FP16        [W(12) b 0 0 0]                                   K = 16
+//   FP8         [W(12) 0 x 20]                                    K = 32
+//   FP16 split  [hiW(12) hib 000 | hiW(12) lob 000 | loW(12) 0000] K = 48
+//   FP8 split   [hiW(12) 0000 | hiW(12) 0000 | loW(12) 0000 | 0 x 16]  K = 64
+// against A0 rows [x(12) 1 000] / [x(12) 0 x 20] / [hi x(12) 1 000 | lo x(12) 1 000]
+// / [hi x(12) 0000 | lo x(12) 0000].
 struct TcLayout {
   int nhid;   // hidden layers (1..3)
-  bool fp8;
-  __host__ __device__ int esz() const { return fp8 ? 1 : 2; }
-  __host__ __device__ int wh_bytes() const { return kHid * kHid * esz(); }   // 64 x 64
-  __host__ __device__ int bth_bytes() const { return fp8 ? 0 : kHid * 16 * 2; }   // 64 x 16 bias tile
-  __host__ __device__ int wo_bytes() const { return kOutPad * kHid * esz(); }   // 16 x 64
-  __host__ __device__ int bto_bytes() const { return fp8 ? 0 : kOutPad * 16 * 2; }  // 16 x 16 bias tile
-  __host__ __device__ int off_w1() const { return 0; }                                // 64 x K1: 2048 B
-  __host__ __device__ int off_wh(int l) const { return 2048 + l * (wh_bytes() + bth_bytes()); }  // l < nhid-1
+  int form;   // TcForm
+  __host__ __device__ bool fp8() const { return form == kF8 || form == kF8Split; }
+  __host__ __device__ bool split() const { return form == kF16Split || form == kF8Split; }
+  __host__ __device__ int esz() const { return fp8() ? 1 : 2; }
+  __host__ __device__ int parts() const { return split() ? 2 : 1; }
+  __host__ __device__ int w1_row() const { return form == kF16Split ? 96 : form == kF8Split ? 64 : 32; }
+  __host__ __device__ int a0_row() const { return form == kF16Split ? 64 : 32; }
+  __host__ __device__ int wh_part() const { return kHid * kHid * esz(); }                // 64 x 64
+  __host__ __device__ int wh_bytes() const { return parts() * wh_part(); }
+  __host__ __device__ int bth_bytes() const { return fp8() ? 0 : kHid * 16 * 2; }       // 64 x 16 bias tile
+  __host__ __device__ int wo_part() const { return kOutPad * kHid * esz(); }             // 16 x 64
+  __host__ __device__ int wo_bytes() const { return parts() * wo_part(); }
+  __host__ __device__ int bto_bytes() const { return fp8() ? 0 : kOutPad * 16 * 2; }    // 16 x 16 bias tile
+  __host__ __device__ int off_w1() const { return 0; }
+  __host__ __device__ int off_wh(int l) const { return kHid * w1_row() + l * (wh_bytes() + bth_bytes()); }  // l < nhid-1
   __host__ __device__ int off_bth(int l) const { return off_wh(l) + wh_bytes(); }
   __host__ __device__ int off_wo() const { return off_wh(nhid - 1); }
   __host__ __device__ int off_bto() const { return off_wo() + wo_bytes(); }
@@ -37,10 +58,12 @@ struct TcLayout {
 };
 
 // Offset of element (row, k) in a K-major operand tile.
-//  no swizzle, 16-byte core matrices of 8 rows: LBO = 128 B (next K chunk), SBO = 256 B (next 8 rows)
-__host__ __device__ inline uint32_t off_interleave(int row, int kbyte) {
-  return (uint32_t)((row >> 3) * 256 + (kbyte >> 4) * 128 + (row & 7) * 16 + (kbyte & 15));
+//  no swizzle, 16-byte core matrices of 8 rows: LBO = 128 B (next K chunk),
+//  SBO = 8 rows x `row` bytes (next 8 rows); `row` = bytes of K per row
+__host__ __device__ inline uint32_t off_ilv(int row, int kbyte, int rowbytes) {
+  return (uint32_t)((row >> 3) * 8 * rowbytes + (kbyte >> 4) * 128 + (row & 7) * 16 + (kbyte & 15));
 }
+__host__ __device__ inline uint32_t off_interleave(int row, int kbyte) { return off_ilv(row, kbyte, 32); }
 //  128-byte swizzle, 128-byte rows (64 f16): atom 8 rows x 128 B, SBO = 1024 B
 __host__ __device__ inline uint32_t off_sw128(int row, int kbyte) {
   return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((kbyte >> 4) ^ (row & 7)) & 7) << 4) + (kbyte & 15));
@@ -101,13 +124,13 @@ struct TcWork {
   int reload;
 };
 
-constexpr int kSlots = 2;          // tile slots per warpgroup (ping-pong)
 constexpr int kStageBytes = 1024;  // per-warp output staging (32 texels x <= 16 halves)
 
 
 struct TcArgs;
-// Launches the decode kernel (any mode) with W warpgroups on `grid` CTAs.
-nbtc_status launch_tc_args(nbtc_context* ctx, const struct TcArgs& p, int nhid, bool fp8, int W, int grid,
+// Launches the decode kernel (any mode) with W warpgroups of `slots` tile
+// slots each on `grid` CTAs.
+nbtc_status launch_tc_args(nbtc_context* ctx, const struct TcArgs& p, int nhid, int form, int W, int slots, int grid,
                            cudaStream_t s);
 
 }  // namespace nbtc

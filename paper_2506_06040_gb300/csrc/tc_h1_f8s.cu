@@ -1,0 +1,11 @@
+// Instantiation unit of the tensor-core decode kernel: 1 hidden layer(s), split E4M3 operands (hi + lo pairs).
+#include "tc_kernel.cuh"
+
+namespace nbtc {
+
+nbtc_status launch_tc_h1_f8s(const TcArgs& p, int W, int slots, int grid, cudaStream_t s) {
+  if (slots != 2) return fail(NBTC_ERR_UNSUPPORTED, "this form runs two tile slots per warpgroup");
+  return W == 3 ? launch_tc_w<1, kF8Split, 3, kModeSingle, 2>(p, grid, s) : launch_tc_w<1, kF8Split, 4, kModeSingle, 2>(p, grid, s);
+}
+
+}  // namespace nbtc

@@ -3,8 +3,9 @@
 
 namespace nbtc {
 
-nbtc_status launch_tc_h2_f16(const TcArgs& p, int W, int grid, cudaStream_t s) {
-  return W == 3 ? launch_tc_w<2, false, 3, kModeSingle>(p, grid, s) : launch_tc_w<2, false, 4, kModeSingle>(p, grid, s);
+nbtc_status launch_tc_h2_f16(const TcArgs& p, int W, int slots, int grid, cudaStream_t s) {
+  if (slots != 2) return fail(NBTC_ERR_UNSUPPORTED, "this form runs two tile slots per warpgroup");
+  return W == 3 ? launch_tc_w<2, kF16, 3, kModeSingle, 2>(p, grid, s) : launch_tc_w<2, kF16, 4, kModeSingle, 2>(p, grid, s);
 }
 
 }  // namespace nbtc

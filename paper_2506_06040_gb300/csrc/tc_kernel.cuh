@@ -1,16 +1,17 @@
 // The tensor-core decode kernel (template; instantiated in tc_h*_*.cu).
 //
-// FP16 or FP8 E4M3 operands, FP32 accumulation in TMEM, FP16 output: the
-// GB300 counterpart of the paper's cooperative-vector MLP (Sec. 4, "Neural
-// inference in G-Buffer pass"); each layer of a 128-texel tile is one chain of
+// FP16 or FP8 E4M3 operands -- single or split into hi + lo pairs (three
+// products per layer) -- FP32 accumulation in TMEM, FP16 output: the GB300
+// counterpart of the paper's cooperative-vector MLP (Sec. 4, "Neural inference
+// in G-Buffer pass"); each layer of a 128-texel tile is one chain of
 // tcgen05.mma with M = 128 texels, N = layer width, weights resident in shared
 // memory.
 //
 // Persistent, warp-specialised CTA (one per SM): W warpgroups of 128 threads
 // (one thread per tile row) compute features and run the epilogues, and
-// W warps (one per warpgroup) issue the MMAs.  Each warpgroup owns two tile slots (TMEM
-// columns + A buffers) and alternates between them, so one slot's SIMT work
-// overlaps the other slot's MMAs.  The CTA walks "chunks" -- runs of tiles of
+// W warps (one per warpgroup) issue the MMAs.  Each warpgroup owns NSL tile
+// slots (TMEM columns + A buffers) and, with two, alternates between them, so
+// one slot's SIMT work overlaps the other slot's MMAs.  The CTA walks "chunks" -- runs of tiles of
 // one material -- and reloads the packed MLP only when the material changes.
 #pragma once
 
@@ -51,14 +52,19 @@ __device__ __forceinline__ int64_t frame_pixel(const TcArgs& p, const WorkChunk&
   return __ldg(p.plist + (c.first + T) * 128 + gt);
 }
 
-// Shared-memory plan.  Per slot: A0 (128 x K1 operand) and Ah (128 x 64
-// operand, also the feature stage's column buffer while no MMA reads it).
+// Shared-memory plan.  Per slot: A0 (128 x K operand of layer 1) and Ah
+// (128 x 64 operand of later layers; split forms: hi tile then lo tile), and
+// the feature stage's column buffer (inside Ah while no MMA reads it).  The
+// FP16 split form lays A0 over the hi tile (A0 is consumed before the first
+// hidden epilogue writes Ah) and the column buffer over the lo tile.
 struct TcSmem {
   int image;       // packed MLP (rounded to 1 KB)
-  int ones;        // 128 x 16 FP16 tile of ones in column 0
+  int ones;        // 128 x 16 FP16 tile of ones in column 0 (split: columns 0 and 1)
   int slots;       // first slot
   int slot;        // bytes per slot
   int a0, ah;      // offsets inside a slot
+  int ah_lo;       // split forms: lo tile of Ah, from ah
+  int colbuf;      // column buffer, inside a slot
   int stage;       // per-warp output staging
   int bars;        // D-ready[NS], weight barrier, MMA-warp drain[W] (room for 2 NS + 1)
   int tslot;       // TMEM address slot
@@ -66,15 +72,25 @@ struct TcSmem {
   int total;
 };
 
-__host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W) {
+__host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W, int NSL) {
   TcSmem s;
-  const int NS = W * kSlots;
+  const int NS = W * NSL;
   s.image = (L.bytes() + 1023) & ~1023;
   s.ones = s.image;
   s.slots = s.ones + 4096;
-  s.a0 = 0;
-  s.ah = 4096;
-  s.slot = 4096 + 16384;
+  if (L.form == kF16Split) {
+    s.a0 = 0;
+    s.ah = 0;
+    s.ah_lo = 16384;
+    s.colbuf = 16384;
+    s.slot = 32768;
+  } else {
+    s.a0 = 0;
+    s.ah = 4096;
+    s.ah_lo = 8192;   // FP8 split: 128 x 64 E4M3 hi, then lo
+    s.colbuf = 4096;
+    s.slot = 4096 + 16384;
+  }
   s.stage = s.slots + NS * s.slot;
   s.bars = s.stage + W * 4 * kStageBytes;
   s.tslot = s.bars + (2 * NS + 1) * 8;
@@ -85,10 +101,10 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W) {
 
 // Warp-specialised persistent kernel: W warpgroups (4 warps, one thread per
 // tile row) compute features and epilogues; warp 4W + g issues the MMAs of
-// warpgroup g.  Each warpgroup owns two tile slots (TMEM columns + A buffers)
-// and alternates between them, so one slot's epilogue runs while the other
-// slot's MMAs run.  Inside a chunk, warpgroup g takes the g-th of W contiguous
-// tile ranges, its slots alternating over it.
+// warpgroup g.  Each warpgroup owns NSL tile slots (TMEM columns + A buffers);
+// with two it alternates between them, so one slot's epilogue runs while the
+// other slot's MMAs run.  Inside a chunk, warpgroup g takes the g-th of W
+// contiguous tile ranges, its slots alternating over it.
 //
 // Hand-offs:
 //   A-ready[q]  named barrier (warpgroup: bar.arrive, its MMA warp: bar.sync,
@@ -101,15 +117,18 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W) {
 // always complete and the kernel always terminates.
 // MODE kModeSingle: one material whose views are kernel parameters; kModeBatch:
 // chunks of many materials (and frame tiles) whose views live in shared memory.
-template <int NHID, bool FP8, int W, int MODE>
+template <int NHID, int FORM, int W, int MODE, int NSL>
 __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
-  constexpr TcLayout L{NHID, FP8};
+  constexpr TcLayout L{NHID, FORM};
+  constexpr bool FP8 = FORM == kF8 || FORM == kF8Split;
+  constexpr bool SPLIT = FORM == kF16Split || FORM == kF8Split;
+  constexpr int kSlots = NSL;
   constexpr int NS = W * kSlots;
   constexpr uint32_t kTmemCols = NS * kHid <= 256 ? 256 : 512;
   static_assert(NS * kHid <= 512, "TMEM holds at most 512 columns");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const TcSmem S = tc_smem(L, W);
+  const TcSmem S = tc_smem(L, W, NSL);
   const uint32_t sbase = smem_u32(smem);
   const int tid = threadIdx.x;
   const int warp = tid / 32, lane = tid % 32;
@@ -134,8 +153,8 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
     work.m.packed = nullptr;
     work.c.mat = -1;
   }
-  if (!FP8 && tid < kTile) {  // ones tile: column 0 = 1.0 (FP16), rest 0
-    sts128(sbase + S.ones + off_interleave(tid, 0), 0x3C00u, 0u, 0u, 0u);
+  if (!FP8 && tid < kTile) {  // ones tile: column 0 (split: columns 0 and 1) = 1.0 (FP16), rest 0
+    sts128(sbase + S.ones + off_interleave(tid, 0), SPLIT ? 0x3C003C00u : 0x3C00u, 0u, 0u, 0u);
     sts128(sbase + S.ones + off_interleave(tid, 16), 0u, 0u, 0u, 0u);
     fence_proxy_async_smem();
   }
@@ -219,9 +238,12 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       constexpr uint32_t ID_OUT = idesc(0, kTile, kOutPad);
       // high words: SBO, version, swizzle; low words: start address, LBO
       const uint32_t hi_int = (uint32_t)(smem_desc(0, 128, 256, kSwzNone) >> 32);
+      const uint32_t hi_a0 = (uint32_t)(smem_desc(0, 128, 8 * L.a0_row(), kSwzNone) >> 32);
+      const uint32_t hi_w1 = (uint32_t)(smem_desc(0, 128, 8 * L.w1_row(), kSwzNone) >> 32);
       const uint32_t hi_w = FP8 ? (uint32_t)(smem_desc(0, 16, 512, kSwz64) >> 32)
                                 : (uint32_t)(smem_desc(0, 16, 1024, kSwz128) >> 32);
       auto lo = [](uint32_t addr, uint32_t lbo) { return (uint32_t)smem_desc(addr, lbo, 0, 0); };
+      auto dsc = [](uint32_t hi, uint32_t lo) { return ((uint64_t)hi << 32) | lo; };
       const uint32_t lo_w1 = lo(sbase + L.off_w1(), 128);
       const uint32_t lo_ones = lo(sbase + S.ones, 128);
       const int64_t g_begin = min((int64_t)m * per_wg, range_end);
@@ -240,27 +262,49 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
               const uint32_t d = tmem_base + (uint32_t)(q * kHid);
               const uint32_t slot = sbase + S.slots + q * S.slot;
               if (l == 0) {
-                const uint64_t ad = ((uint64_t)hi_int << 32) | lo(slot + S.a0, 128);
-                const uint64_t bd = ((uint64_t)hi_int << 32) | lo_w1;
-                if constexpr (FP8) mma_f8(d, ad, bd, ID_HID, 0);
-                else mma_f16(d, ad, bd, ID_HID, 0);
+                // K chunks of 32 bytes (16 FP16 / 32 E4M3), 256 bytes apart in
+                // the no-swizzle layout
+                const uint32_t la = lo(slot + S.a0, 128);
+                if constexpr (FORM == kF16Split) {
+                  mma_f16(d, dsc(hi_a0, la), dsc(hi_w1, lo_w1), ID_HID, 0);                // hi x . hi W + hi b
+                  mma_f16(d, dsc(hi_a0, la + 16), dsc(hi_w1, lo_w1 + 16), ID_HID, 1);      // lo x . hi W + lo b
+                  mma_f16(d, dsc(hi_a0, la), dsc(hi_w1, lo_w1 + 32), ID_HID, 1);           // hi x . lo W
+                } else if constexpr (FORM == kF8Split) {
+                  mma_f8(d, dsc(hi_a0, la), dsc(hi_w1, lo_w1), ID_HID, 0);                 // [hi x | lo x] . hi W
+                  mma_f8(d, dsc(hi_a0, la), dsc(hi_w1, lo_w1 + 16), ID_HID, 1);            // [hi x | lo x] . [lo W | 0]
+                } else if constexpr (FP8) {
+                  mma_f8(d, dsc(hi_int, la), dsc(hi_int, lo_w1), ID_HID, 0);
+                } else {
+                  mma_f16(d, dsc(hi_int, la), dsc(hi_int, lo_w1), ID_HID, 0);
+                }
               } else {
                 const bool last = l == NHID;
                 const uint32_t id = last ? ID_OUT : ID_HID;
                 const uint32_t lo_a = lo(slot + S.ah, 16);
                 const uint32_t lo_b = lo(sbase + (last ? L.off_wo() : L.off_wh(l - 1)), 16);
+                // lo halves of A and W (split forms), in 16-byte units
+                const uint32_t da = (uint32_t)S.ah_lo >> 4;
+                const uint32_t db = (uint32_t)(last ? L.wo_part() : L.wh_part()) >> 4;
                 if constexpr (FP8) {
 #pragma unroll
-                  for (int kk = 0; kk < 2; ++kk)
-                    mma_f8(d, ((uint64_t)hi_w << 32) | (lo_a + 2 * kk), ((uint64_t)hi_w << 32) | (lo_b + 2 * kk), id,
-                           kk > 0);
+                  for (int kk = 0; kk < 2; ++kk) {
+                    mma_f8(d, dsc(hi_w, lo_a + 2 * kk), dsc(hi_w, lo_b + 2 * kk), id, kk > 0);
+                    if constexpr (SPLIT) {
+                      mma_f8(d, dsc(hi_w, lo_a + da + 2 * kk), dsc(hi_w, lo_b + 2 * kk), id, 1);
+                      mma_f8(d, dsc(hi_w, lo_a + 2 * kk), dsc(hi_w, lo_b + db + 2 * kk), id, 1);
+                    }
+                  }
                 } else {
                   const uint32_t lo_bt = lo(sbase + (last ? L.off_bto() : L.off_bth(l - 1)), 128);
-                  mma_f16(d, ((uint64_t)hi_int << 32) | lo_ones, ((uint64_t)hi_int << 32) | lo_bt, id, 0);
+                  mma_f16(d, dsc(hi_int, lo_ones), dsc(hi_int, lo_bt), id, 0);
 #pragma unroll
-                  for (int kk = 0; kk < 4; ++kk)
-                    mma_f16(d, ((uint64_t)hi_w << 32) | (lo_a + 2 * kk), ((uint64_t)hi_w << 32) | (lo_b + 2 * kk), id,
-                            1);
+                  for (int kk = 0; kk < 4; ++kk) {
+                    mma_f16(d, dsc(hi_w, lo_a + 2 * kk), dsc(hi_w, lo_b + 2 * kk), id, 1);
+                    if constexpr (SPLIT) {
+                      mma_f16(d, dsc(hi_w, lo_a + da + 2 * kk), dsc(hi_w, lo_b + 2 * kk), id, 1);
+                      mma_f16(d, dsc(hi_w, lo_a + 2 * kk), dsc(hi_w, lo_b + db + 2 * kk), id, 1);
+                    }
+                  }
                 }
               }
               mma_commit(dbar0 + q * 8);
@@ -297,7 +341,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
             // tile's last MMA (which read it) has completed
             const uint32_t t = (uint32_t)(work.c.first + T), H = (uint32_t)D.grid_h;
             const uint32_t cb = fastdiv(t, hdiv);
-            strip_features<kTile>(D, (int)(t - cb * H), (int)cb * kTile, gt, a0 - S.a0 + S.ah, bar_id, cache, f);
+            strip_features<kTile>(D, (int)(t - cb * H), (int)cb * kTile, gt, a0 - S.a0 + S.colbuf, bar_id, cache, f);
           } else {
             const int64_t tex = (work.c.first + T) * kTile + gt;
             direct_features(D, tex < D.n ? tex : D.n - 1, f);
@@ -312,12 +356,21 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
           else
             trilinear_features(work.m, uv.x, uv.y, __ldg(p.flod + pq), f);
         }
-        if constexpr (!FP8) {
+        if constexpr (FORM == kF16) {
           sts128(a0 + off_interleave(gt, 0), cvt_f16x2(f[0], f[1]), cvt_f16x2(f[2], f[3]), cvt_f16x2(f[4], f[5]),
                  cvt_f16x2(f[6], f[7]));
           sts128(a0 + off_interleave(gt, 16), cvt_f16x2(f[8], f[9]), cvt_f16x2(f[10], f[11]),
                  0x3C00u /* k = 12: 1.0 for the bias */, 0u);
-        } else {
+        } else if constexpr (FORM == kF16Split) {
+          uint32_t h[6], r[6];
+#pragma unroll
+          for (int i = 0; i < 6; ++i) split_f16x2(f[2 * i], f[2 * i + 1], h[i], r[i]);
+          const int R = L.a0_row();
+          sts128(a0 + off_ilv(gt, 0, R), h[0], h[1], h[2], h[3]);
+          sts128(a0 + off_ilv(gt, 16, R), h[4], h[5], 0x3C00u /* k = 12: 1.0 for hi(b) */, 0u);
+          sts128(a0 + off_ilv(gt, 32, R), r[0], r[1], r[2], r[3]);
+          sts128(a0 + off_ilv(gt, 48, R), r[4], r[5], 0x3C00u /* k = 28: 1.0 for lo(b) */, 0u);
+        } else if constexpr (FORM == kF8) {
           const float is = alpha[NHID + 1];  // 1 / input scale
           uint32_t w[3];
 #pragma unroll
@@ -326,6 +379,19 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
                    ((uint32_t)cvt_e4m3x2(f[4 * i + 2] * is, f[4 * i + 3] * is) << 16);
           sts128(a0 + off_interleave(gt, 0), w[0], w[1], w[2], 0u);
           sts128(a0 + off_interleave(gt, 16), 0u, 0u, 0u, 0u);
+        } else {
+          const float is = alpha[NHID + 1];  // 1 / input scale
+          uint32_t h[3], r[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            uint16_t h0, r0, h1, r1;
+            split_e4m3x2(cvt_f16x2(f[4 * i] * is, f[4 * i + 1] * is), h0, r0);
+            split_e4m3x2(cvt_f16x2(f[4 * i + 2] * is, f[4 * i + 3] * is), h1, r1);
+            h[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            r[i] = (uint32_t)r0 | ((uint32_t)r1 << 16);
+          }
+          sts128(a0 + off_interleave(gt, 0), h[0], h[1], h[2], 0u);
+          sts128(a0 + off_interleave(gt, 16), r[0], r[1], r[2], 0u);
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -350,7 +416,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
         for (int part = 0; part < kParts; ++part) {
           uint32_t r[kPc];
           tmem_ld32_wait(taddr + kPc * part, r);
-          if constexpr (!FP8) {
+          if constexpr (FORM == kF16) {
 #pragma unroll
             for (int c = 0; c < kPc / 8; ++c) {
               const int j = 8 * c;
@@ -360,10 +426,22 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
                      cvt_relu_f16x2(__uint_as_float(r[j + 4]), __uint_as_float(r[j + 5])),
                      cvt_relu_f16x2(__uint_as_float(r[j + 6]), __uint_as_float(r[j + 7])));
             }
+          } else if constexpr (FORM == kF16Split) {
+#pragma unroll
+            for (int c = 0; c < kPc / 8; ++c) {
+              const int j = 8 * c;
+              uint32_t h[4], lw[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                split_relu_f16x2(__uint_as_float(r[j + 2 * e]), __uint_as_float(r[j + 2 * e + 1]), h[e], lw[e]);
+              const uint32_t o = off_sw128(gt, 16 * (part * (kPc / 8) + c));
+              sts128(ah + o, h[0], h[1], h[2], h[3]);
+              sts128(ah + S.ah_lo + o, lw[0], lw[1], lw[2], lw[3]);
+            }
           } else {
 #pragma unroll
             for (int c = 0; c < kPc / 16; ++c) {
-              uint32_t w[4];
+              uint32_t w[4], wl[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 // scale and bias as packed FMAs (two IEEE FP32 FMAs each)
@@ -373,9 +451,19 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
                                              make_float2(alp, alp), make_float2(bb.x, bb.y));
                 const float2 v1 = __ffma2_rn(make_float2(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])),
                                              make_float2(alp, alp), make_float2(bb.z, bb.w));
-                w[e] = (uint32_t)cvt_relu_e4m3x2(v0.x, v0.y) | ((uint32_t)cvt_relu_e4m3x2(v1.x, v1.y) << 16);
+                if constexpr (FORM == kF8) {
+                  w[e] = (uint32_t)cvt_relu_e4m3x2(v0.x, v0.y) | ((uint32_t)cvt_relu_e4m3x2(v1.x, v1.y) << 16);
+                } else {
+                  uint16_t h0, r0, h1, r1;
+                  split_e4m3x2(cvt_relu_f16x2(v0.x, v0.y), h0, r0);
+                  split_e4m3x2(cvt_relu_f16x2(v1.x, v1.y), h1, r1);
+                  w[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                  wl[e] = (uint32_t)r0 | ((uint32_t)r1 << 16);
+                }
               }
-              sts128(ah + off_sw64(gt, 16 * (part * (kPc / 16) + c)), w[0], w[1], w[2], w[3]);
+              const uint32_t o = off_sw64(gt, 16 * (part * (kPc / 16) + c));
+              sts128(ah + o, w[0], w[1], w[2], w[3]);
+              if constexpr (SPLIT) sts128(ah + S.ah_lo + o, wl[0], wl[1], wl[2], wl[3]);
             }
           }
         }
@@ -449,8 +537,9 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
         }
       };
 
-      if (g_begin < g_end) start_tile(0, g_begin);
-      if (g_begin + 1 < g_end) start_tile(1, g_begin + 1);
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s)  // prime each of this warpgroup's own slots
+        if (g_begin + s < g_end) start_tile(s, g_begin + s);
       for (int64_t base = g_begin; base < g_end; base += kSlots) {
         const bool two = base + 1 < g_end;
 #pragma unroll
@@ -502,10 +591,10 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
 }
 
 
-template <int NHID, bool FP8, int W, int MODE>
+template <int NHID, int FORM, int W, int MODE, int NSL>
 nbtc_status launch_tc_w(const TcArgs& p, int grid, cudaStream_t s) {
-  const TcSmem S = tc_smem(TcLayout{NHID, FP8}, W);
-  auto kern = k_decode_tc<NHID, FP8, W, MODE>;
+  const TcSmem S = tc_smem(TcLayout{NHID, FORM}, W, NSL);
+  auto kern = k_decode_tc<NHID, FORM, W, MODE, NSL>;
   nbtc_status st =
       cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S.total), "smem attribute");
   if (st) return st;

@@ -40,12 +40,16 @@ def test_binding_covers_header():
 
 def test_struct_layouts_match_c():
     """Every ctypes struct of the binding has the C compiler's size and every
-    field the C compiler's offset."""
+    field the C compiler's offset; the precision codes match the header's."""
     from paper_2506_06040_gb300 import _abi
     pairs = [("nbtc_level", _abi.Level), ("nbtc_latents", _abi.Latents), ("nbtc_mlp", _abi.Mlp),
              ("nbtc_train_args", _abi.TrainArgs), ("nbtc_batch_material", _abi.BatchMaterial),
              ("nbtc_frame", _abi.Frame), ("nbtc_batch_info", _abi.BatchInfo)]
     lines, want = [], []
+    for cname, val in [("NBTC_FP32", _abi.FP32), ("NBTC_FP16", _abi.FP16), ("NBTC_FP8_E4M3", _abi.FP8_E4M3),
+                       ("NBTC_FP16_SPLIT", _abi.FP16_SPLIT), ("NBTC_FP8_E4M3_SPLIT", _abi.FP8_E4M3_SPLIT)]:
+        lines.append(f'  printf("%d\\n", (int){cname});')
+        want.append(val)
     for cname, cls in pairs:
         lines.append(f'  printf("%zu\\n", sizeof({cname}));')
         want.append(ctypes.sizeof(cls))
@@ -78,6 +82,15 @@ def test_host_only_checks(lib):
     assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), 0, ctypes.byref(n)) == _abi.ERR_INVALID_ARG  # NULL weights
     m.weights, m.biases = 16, 16
     assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), _abi.FP32, ctypes.byref(n)) == _abi.OK and n.value == 0
+    sizes = {}
+    for prec in (_abi.FP16, _abi.FP8_E4M3, _abi.FP16_SPLIT, _abi.FP8_E4M3_SPLIT):
+        assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), prec, ctypes.byref(n)) == _abi.OK
+        sizes[prec] = n.value
+        assert n.value % 16 == 0
+    # the split forms store hi and lo of every weight tile
+    assert sizes[_abi.FP16_SPLIT] > sizes[_abi.FP16] > sizes[_abi.FP8_E4M3]
+    assert sizes[_abi.FP8_E4M3_SPLIT] > sizes[_abi.FP8_E4M3]
+    assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), 5, ctypes.byref(n)) == _abi.ERR_INVALID_ARG
     m.num_layers = 7
     assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), _abi.FP32, ctypes.byref(n)) == _abi.ERR_INVALID_ARG
     assert b"num_layers" in lib.nbtc_last_error()

@@ -8,21 +8,15 @@ import torch
 import oracle
 import synth
 from gpu_util import require_gpu
-from test_decode_tc_gpu import _check
+import tc_parity as tp
 
 pytestmark = pytest.mark.gpu
 NAN16 = 0x7E00
-# Share of outputs within one FP16 ulp of the emulator.  Trilinear features take
-# more FP32 steps than the single-level path, so an FP32 feature lands on the
-# other side of an FP16 rounding boundary more often; the per-output error bound
-# (checked first) is unchanged.  A systematic fault would miss this by far.
-FRAC = 0.95
-
-
-def FEATURE_BOUND(n):
-    """Latent features lie in [0, 1], so the network run on ones bounds the
-    magnitudes that enter the kernel-vs-emulator error bound."""
-    return np.ones((n, 12))
+# FP32 error of the kernels' features (standard deviation of the interval's
+# error model): trilinear features blend two bilinear samples; anisotropic ones
+# average up to 16 trilinear probes
+SIGMA_TRILINEAR = 2.0 ** -21
+SIGMA_ANISO = 2.0 ** -20
 
 
 @pytest.fixture(scope="module")
@@ -42,8 +36,7 @@ def ctx(nb):
 def _grid_check(mat, S, got, idx):
     uv = np.stack([oracle.sample.grid_coord(idx % S, S), oracle.sample.grid_coord(idx // S, S)], -1).astype(np.float64)
     lod = np.full(len(idx), -64.0)   # mip 0 of every level
-    emu = oracle.frame.decode_pixels_direct(mat, uv, lod, "fp16")
-    _check(got, emu, mat, FEATURE_BOUND(len(idx)), 2.0 ** -10, FRAC)
+    tp.check_interval(got, mat, oracle.frame.pixel_features_direct(mat, uv, lod), "fp16", what="material grid")
 
 
 def _frame_tensors(bw, nout=9):
@@ -64,8 +57,8 @@ def _frame_check(bw, out, pixels):
     for m in np.unique(ids[ids >= 0]):
         sel = ids == m
         mat = bw.materials[m]
-        emu = oracle.frame.decode_pixels_direct(mat, uv[sel], lod[sel], "fp16")
-        _check(got[sel], emu, mat, FEATURE_BOUND(int(sel.sum())), 2.0 ** -10, FRAC)
+        x = oracle.frame.pixel_features_direct(mat, uv[sel], lod[sel])
+        tp.check_interval(got[sel], mat, x, "fp16", sigma_x=SIGMA_TRILINEAR, what=f"frame material {m}")
     raw = out.view(torch.int16).view(-1, 9)[torch.from_numpy(pixels).cuda()].cpu().numpy()
     assert np.all(raw[ids < 0] == NAN16)  # pixels without a material are left untouched
 
@@ -141,8 +134,8 @@ def test_frame_anisotropic_filter_all_pixels(nb, ctx, max_aniso):
         sel = ids == m
         mat = bw.materials[m]
         mips = [oracle.frame.level_mips_rgb(lv) for lv in mat.levels]
-        emu = oracle.frame.decode_pixels_aniso(mat, mips, uv[sel], duv[sel], bias[sel], max_aniso, "fp16")
-        _check(got[sel], emu, mat, FEATURE_BOUND(int(sel.sum())), 2.0 ** -10, FRAC)
+        x = oracle.frame.aniso_features(mat, mips, uv[sel], duv[sel], bias[sel], max_aniso)
+        tp.check_interval(got[sel], mat, x, "fp16", sigma_x=SIGMA_ANISO, what=f"aniso frame material {m}")
     plan.close()
 
 
@@ -227,8 +220,8 @@ def test_full_size_anisotropic_and_lit_frames(nb, ctx):
         sel = ids == m
         mat = bw.materials[m]
         mips = [oracle.frame.level_mips_rgb(lv) for lv in mat.levels]
-        emu = oracle.frame.decode_pixels_aniso(mat, mips, uv[sel], duv[sel], bias[sel], 16, "fp16")
-        _check(got[sel], emu, mat, FEATURE_BOUND(int(sel.sum())), 2.0 ** -10, FRAC)
+        x = oracle.frame.aniso_features(mat, mips, uv[sel], duv[sel], bias[sel], 16)
+        tp.check_interval(got[sel], mat, x, "fp16", sigma_x=SIGMA_ANISO, what=f"aniso frame material {m}")
     plan.close()
     del fa
     # lit

@@ -135,20 +135,21 @@ def test_decode_mlp_shapes(nb, ctx, dims, layout):
     assert max_abs(y.cpu().numpy(), ref) <= TOL_FP32
 
 
-def test_decode_config1_full_size_sampled(nb, ctx):
-    """The 4096^2 decode in the launch configuration the benchmark times, checked
-    on 65,536 random texels plus the first and last rows and columns."""
+def test_decode_config1_full_size_every_texel(nb, ctx):
+    """The 4096^2 decode in the launch configuration the benchmark times: every one
+    of its 16.8M texels x 9 channels within 1e-5 of the FP64 oracle (the oracle
+    runs on row bands in one spawned worker per host core)."""
+    import tc_parity as tp
     wl = synth.decode_workload(1)
     mat = nb.Material.from_synth(wl.material)
     y = nb.decode(ctx, mat, grid=(4096, 4096))
     ctx.sync()
-    rng = np.random.default_rng(5)
-    idx = np.concatenate([rng.integers(0, 4096 * 4096, 65536), np.arange(4096), 4096 * 4095 + np.arange(4096),
-                          np.arange(4096) * 4096, np.arange(4096) * 4096 + 4095])
-    ref = oracle.decode.decode_grid(wl.material, 4096, 4096, idx)
-    got = y[torch.from_numpy(idx).cuda()].cpu().numpy()
-    assert max_abs(got, ref) <= TOL_FP32
-    assert torch.isfinite(y).all()
+    got = y.view(4096, 4096, 9).cpu().numpy()
+    with tp.pool() as p:
+        err = np.max(p.map(tp.band_fp32, [(1, r, n, got[r:r + n].reshape(-1, 9)) for r, n in tp.bands(4096, 64)]),
+                     axis=0)
+    print("FP32 4096^2 per-channel max abs error vs FP64 (every texel):", np.round(err, 8).tolist())
+    assert np.all(err <= TOL_FP32), err
 
 
 def test_zero_and_one_texel(nb, ctx):

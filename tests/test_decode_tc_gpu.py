@@ -1,12 +1,14 @@
-"""GPU parity of the tensor-core forms (tcgen05, FP16 / FP8 E4M3 operands, FP32
-accumulation, FP16 output) against the oracle's quantisation emulator, and
-their error against the FP64 oracle, through the C ABI."""
+"""GPU parity of the single-rounding tensor-core forms (tcgen05, FP16 / FP8 E4M3
+operands, FP32 accumulation, FP16 output) against the oracle's quantisation
+emulator -- every output inside its admissible interval -- and their error
+against the FP64 oracle, through the C ABI."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import synth
+import tc_parity as tp
 from gpu_util import require_gpu
 
 pytestmark = pytest.mark.gpu
@@ -18,29 +20,14 @@ def _grid_uv(idx, gw, gh):
             oracle.sample.grid_coord(idx // gw, gh).astype(np.float64))
 
 
-def ulp16(x):
-    """Spacing of binary16 numbers at |x| (2^-24 below the normal range)."""
-    ax = np.maximum(np.abs(np.asarray(x, dtype=np.float64)), 2.0 ** -14)
-    return np.ldexp(1.0, np.floor(np.log2(ax)).astype(np.int64) - 10)
+def _check(got, material, x, form="fp16", scales=None):
+    """Every output inside the emulator's admissible interval (the emulated value
+    wherever no rounding decision is in doubt); returns statistics."""
+    return tp.check_interval(got, material, x, form, scales)
 
 
-# Kernel vs emulator.  The two differ only where an FP32 intermediate of the kernel
-# (tensor-core accumulation, bias add, FP32 features) lands on the other side of a
-# rounding boundary of a hidden activation than the exact value does: that
-# activation then differs by one unit of the narrow format.  To first order such
-# flips move output c by at most  u * sum_l |W_L| ... |W_(l+1)| |h_l|,  bounded by
-#   u * NHID * absnet(x),   absnet = the network run on |W|, |b|, |x|,
-# with u = 2^-10 (FP16 unit) or 2^-3 (E4M3 unit).  The output rounding adds its own
-# few FP16 ulps.  Statistically almost every output must still match to an ulp.
-TOL_ULPS_FP16 = 4
-FRAC_1ULP_FP16 = 0.99
-
-
-def absnet(material, x):
-    h = np.abs(np.asarray(x, dtype=np.float64))
-    for w, b in zip(material.mlp.weights, material.mlp.biases):
-        h = h @ np.abs(w.astype(np.float64)).T + np.abs(b.astype(np.float64))
-    return h
+def _check_fp16(got, material, x):
+    return _check(got, material, x, "fp16")
 
 
 @pytest.fixture(scope="module")
@@ -68,21 +55,6 @@ def _fp16_case(nb, ctx, wl, grid=None, uv=None):
     return y.float().cpu().numpy().astype(np.float64)
 
 
-def _check(got, emu, material, x, unit, frac_1ulp):
-    err = np.abs(got - emu)
-    assert np.all(np.isfinite(got))
-    nhid = len(material.mlp.weights) - 1
-    bound = TOL_ULPS_FP16 * ulp16(emu) + unit * nhid * absnet(material, x)
-    assert np.all(err <= bound), float((err / bound).max())
-    frac = float(np.mean(err <= ulp16(emu) + 2.0 ** -24))
-    assert frac >= frac_1ulp, frac
-    return float(err.max()), frac
-
-
-def _check_fp16(got, emu, material, x):
-    return _check(got, emu, material, x, 2.0 ** -10, FRAC_1ULP_FP16)
-
-
 def _grid_x(material, gw, gh, idx=None):
     if idx is None:
         idx = np.arange(gw * gh)
@@ -94,8 +66,7 @@ def _grid_x(material, gw, gh, idx=None):
 def test_fp16_grid_footprint(nb, ctx, dims):
     wl = synth.small_decode_workload(512, dims, seed=300 + len(dims))
     got = _fp16_case(nb, ctx, wl, grid=(512, 96))
-    emu = oracle.decode.decode_grid(wl.material, 512, 96, precision="fp16")
-    _check_fp16(got, emu, wl.material, _grid_x(wl.material, 512, 96))
+    print(dims, _check_fp16(got, wl.material, _grid_x(wl.material, 512, 96)))
 
 
 @pytest.mark.parametrize("gw,gh,levels", [(1024, 768, None), (384, 1024, [384, 192, 96, 48])])
@@ -111,16 +82,14 @@ def test_fp16_grid_long_strips(nb, ctx, gw, gh, levels):
     features more often than the 1-ulp criterion assumes."""
     wl = synth.small_decode_workload(1024, [12, 64, 64, 64, 9], seed=330 + gh, level_sides=levels)
     got = _fp16_case(nb, ctx, wl, grid=(gw, gh))
-    emu = oracle.decode.decode_grid(wl.material, gw, gh, precision="fp16")
-    _check_fp16(got, emu, wl.material, _grid_x(wl.material, gw, gh))
+    _check_fp16(got, wl.material, _grid_x(wl.material, gw, gh))
 
 
 @pytest.mark.parametrize("gw,gh", [(200, 72), (130, 3), (7, 5), (128, 1), (256, 2), (65536, 1), (1, 4096)])
 def test_fp16_ragged(nb, ctx, gw, gh):
     wl = synth.small_decode_workload(256, [12, 64, 64, 9], seed=310)
     got = _fp16_case(nb, ctx, wl, grid=(gw, gh))
-    emu = oracle.decode.decode_grid(wl.material, gw, gh, precision="fp16")
-    _check_fp16(got, emu, wl.material, _grid_x(wl.material, gw, gh))
+    _check_fp16(got, wl.material, _grid_x(wl.material, gw, gh))
 
 
 @pytest.mark.parametrize("address", ["clamp", "wrap"])
@@ -128,37 +97,31 @@ def test_fp16_uv_list(nb, ctx, address):
     wl = synth.small_decode_workload(256, [12, 64, 64, 64, 9], seed=320, address=address)
     uv = synth.random_uv(321, 5000 * 2 + 77, lo=-0.25, hi=1.25)
     got = _fp16_case(nb, ctx, wl, uv=uv)
-    emu = oracle.decode.decode_uv(wl.material, uv, precision="fp16")
     x = oracle.decode.features_at(wl.material, uv[:, 0].astype(np.float64), uv[:, 1].astype(np.float64))
-    _check_fp16(got, emu, wl.material, x)
+    _check_fp16(got, wl.material, x)
 
 
-def test_fp16_full_size_sampled_and_error_budget(nb, ctx):
-    """The 4096^2, 12-64-64-64-9 FP16 decode in the benchmark's launch configuration:
-    65,536 random texels and the border rows against the emulator; per-channel max abs
-    error against the FP64 oracle reported and bounded."""
+def test_fp16_full_size_every_texel(nb, ctx):
+    """The 4096^2, 12-64-64-64-9 FP16 decode in the benchmark's launch
+    configuration: every one of its 16.8M texels inside its admissible interval;
+    per-channel max abs error against the FP64 oracle reported for kernel and
+    emulator (the single FP16 rounding costs ~3e-3 here, above 2e-3: the split
+    form is the one that meets that bound) and the kernel's bounded by the
+    emulator's plus one FP16 unit at the largest output."""
     wl = synth.decode_workload(2)
     mat = nb.Material.from_synth(wl.material)
     packed = nb.pack_mlp(ctx, mat, nb.FP16)
     y = nb.decode(ctx, mat, nb.FP16, packed, grid=(4096, 4096))
     ctx.sync()
-    rng = np.random.default_rng(6)
-    idx = np.concatenate([rng.integers(0, 4096 * 4096, 65536), np.arange(4096), 4096 * 4095 + np.arange(4096)])
-    got = y[torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
-    tex = [oracle.decode.level_rgb(lv) for lv in wl.material.levels]
-    emu = oracle.decode.decode_grid(wl.material, 4096, 4096, idx, precision="fp16", tex=tex)
-    x = oracle.decode.features_at(wl.material, *_grid_uv(idx, 4096, 4096), tex)
-    e_emu, frac = _check_fp16(got, emu, wl.material, x)
-    ref = oracle.decode.decode_grid(wl.material, 4096, 4096, idx, tex=tex)
-    per_channel = np.abs(got - ref).max(axis=0)
-    emu_channel = np.abs(emu - ref).max(axis=0)
-    print(f"FP16 kernel vs emulator: max {e_emu:.3g}, {frac:.5f} within 1 ulp")
-    print("FP16 per-channel max abs error vs FP64, kernel:  ", np.round(per_channel, 6).tolist())
-    print("FP16 per-channel max abs error vs FP64, emulator:", np.round(emu_channel, 6).tolist())
-    # The FP16 operands themselves cost ~3.3e-3 on this He-initialised network (the
-    # emulator's floor, above the 2e-3 target); the kernel must add nothing beyond it.
-    assert np.all(per_channel <= emu_channel + 2.0 ** -11)
-    assert torch.isfinite(y).all()
+    got = y.view(4096, 4096, 9).cpu().numpy()
+    with tp.pool() as p:
+        res = p.map(tp.band_form, [(2, "fp16", None, r, n, got[r:r + n].reshape(-1, 9)) for r, n in tp.bands(4096, 32)])
+    kern = np.max([r[1] for r in res], axis=0)
+    emu = np.max([r[2] for r in res], axis=0)
+    print("FP16 4096^2: kernel == emulator on", np.mean([r[0]["equal"] for r in res]), "of outputs")
+    print("FP16 per-channel max abs error vs FP64, kernel:  ", np.round(kern, 6).tolist())
+    print("FP16 per-channel max abs error vs FP64, emulator:", np.round(emu, 6).tolist())
+    assert np.all(kern <= emu + 2.0 ** -9)
 
 
 def _fp8_setup(nb, ctx, wl, gw, gh):
@@ -182,8 +145,7 @@ def test_fp16_hidden_width_sweep(nb, ctx, dims, layout):
     lv = [side // 4, side // 8, side // 16, side // 32] if layout == "B" else [side // 4, side // 4, side // 8, side // 8]
     wl = synth.small_decode_workload(side, dims, seed=340 + dims[1] + len(dims), level_sides=lv)
     got = _fp16_case(nb, ctx, wl, grid=(side, 96))
-    emu = oracle.decode.decode_grid(wl.material, side, 96, precision="fp16")
-    _check_fp16(got, emu, wl.material, _grid_x(wl.material, side, 96))
+    _check_fp16(got, wl.material, _grid_x(wl.material, side, 96))
 
 
 @pytest.mark.parametrize("dims", [[12, 64, 9], [12, 64, 64, 64, 9], [12, 32, 9]])
@@ -194,10 +156,9 @@ def test_fp8_grid(nb, ctx, dims):
     ctx.sync()
     got = y.float().cpu().numpy().astype(np.float64)
     emu = oracle.decode.decode_grid(wl.material, 512, 128, precision="fp8", fp8=scales)
-    e, frac = _check(got, emu, wl.material, _grid_x(wl.material, 512, 128), 2.0 ** -3, 0.99)
+    st = _check(got, wl.material, _grid_x(wl.material, 512, 128), "fp8", scales)
     ref = oracle.decode.decode_grid(wl.material, 512, 128)
-    print(f"FP8 {dims}: kernel vs emulator max {e:.3g} ({frac:.5f} within 1 ulp16); "
-          f"per-channel max abs vs FP64 kernel {np.round(np.abs(got - ref).max(0), 4).tolist()} "
+    print(f"FP8 {dims}: {st}; per-channel max abs vs FP64 kernel {np.round(np.abs(got - ref).max(0), 4).tolist()} "
           f"emulator {np.round(np.abs(emu - ref).max(0), 4).tolist()}")
 
 
@@ -212,9 +173,8 @@ def test_fp8_full_size_sampled(nb, ctx):
     idx = np.concatenate([rng.integers(0, 4096 * 4096, 65536), np.arange(4096), 4096 * 4095 + np.arange(4096)])
     got = y[torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
     tex = [oracle.decode.level_rgb(lv) for lv in wl.material.levels]
-    emu = oracle.decode.decode_grid(wl.material, 4096, 4096, idx, precision="fp8", fp8=scales, tex=tex)
     x = oracle.decode.features_at(wl.material, *_grid_uv(idx, 4096, 4096), tex)
-    _check(got, emu, wl.material, x, 2.0 ** -3, 0.99)
+    _check(got, wl.material, x, "fp8", scales)
 
 
 def test_fp8_calibration_matches_oracle(nb, ctx):

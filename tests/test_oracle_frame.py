@@ -112,7 +112,9 @@ def test_aniso_symmetries_and_constant_texture():
     bias = rng.uniform(0, 2, 400).astype(np.float32)
     x = frame.aniso_features(mat, mips, uv, duv, bias, 16)
     # the probes are symmetric about uv: negating the derivatives changes nothing
-    assert np.max(np.abs(frame.aniso_features(mat, mips, uv, -duv, bias, 16) - x)) < 1e-12
+    # but the FP32 roundings of the probe coordinates (a shift of the offsets,
+    # e.g. i / N - 1/2, breaks the symmetry by ~1e-3)
+    assert np.max(np.abs(frame.aniso_features(mat, mips, uv, -duv, bias, 16) - x)) < 2.0 ** -14
     # which screen axis carries the major derivative does not matter
     sw = duv[:, [2, 3, 0, 1]]
     assert np.max(np.abs(frame.aniso_features(mat, mips, uv, sw, bias, 16) - x)) < 1e-12
