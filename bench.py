@@ -60,9 +60,8 @@ def _hbm(algo_bytes: int, ms: float, peaks: dict) -> dict:
 def _profiled_traffic(profile: str):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
     kernel, as recorded in profiles/<profile>.md from one ncu capture, or None
-    when the kernel's sources changed since (the summary stores the SHA-256 of
-    the source files it was captured from) or the summary is missing."""
-    import hashlib
+    when the kernel's sources or any library header changed since (the summary
+    stores the SHA-256 of its sources and the headers) or the summary is missing."""
     path = os.path.join(ROOT, "profiles", profile + ".md")
     if not os.path.exists(path):
         return None
@@ -73,19 +72,66 @@ def _profiled_traffic(profile: str):
             fields[k.strip()] = v.strip().strip("`")
     try:
         srcs = [s.strip() for s in fields["sources"].split(",")]
-        h = hashlib.sha256()
-        for src in srcs:
-            h.update(open(os.path.join(ROOT, src), "rb").read())
-        if h.hexdigest() != fields["source_sha256"]:
+        if _source_hash(srcs) != fields["source_sha256"]:
             return None
         return int(fields["traffic_bytes_per_launch"])
     except (KeyError, OSError, ValueError):
         return None
 
 
+def _source_hash(srcs) -> str:
+    """SHA-256 of the listed source files followed by every header the library's
+    kernels compile against (csrc/*.h, csrc/*.cuh, include/*.h), in name order:
+    a change to any of them retires a recorded traffic figure."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    hdrs = sorted(glob.glob(os.path.join(ROOT, "paper_2506_06040_gb300", "csrc", "*.h")) +
+                  glob.glob(os.path.join(ROOT, "paper_2506_06040_gb300", "csrc", "*.cuh")) +
+                  glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for path in [os.path.join(ROOT, src) for src in srcs] + hdrs:
+        h.update(open(path, "rb").read())
+    return h.hexdigest()
+
+
 def _fp32_peak_tflops(sm_count: int, mhz: float) -> float:
-    """FFMA peak: SMs x 128 FP32 lanes x 2 FLOP x clock."""
+    """FFMA peak from unit counts: SMs x 128 FP32 lanes x 2 FLOP x clock (context)."""
     return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def measure_ffma_peak(nb, ctx, stream, sm_count: int) -> dict:
+    """Measured FP32 FFMA throughput: the library's probe kernel (16 independent
+    FMA chains per thread, 8 CTAs of 256 threads per SM, plain and packed
+    FP32x2 FMAs), a few ms per launch, best of 10 per variant, CUDA events on the
+    launching stream."""
+    import ctypes
+
+    import torch
+
+    from paper_2506_06040_gb300._abi import check
+    out = torch.zeros(1, dtype=torch.float32, device="cuda")
+    flop = ctypes.c_double()
+    best = {}
+    for packed in (0, 1):
+        launch = lambda: check(ctx.lib.nbtc_probe_ffma(ctx.handle, 8 * sm_count, 8192, packed,
+                                                           ctypes.c_void_p(out.data_ptr()), ctypes.byref(flop),
+                                                           ctypes.c_void_p(stream.cuda_stream)))
+        for _ in range(3):
+            launch()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(10):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            launch()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        best["packed" if packed else "plain"] = flop.value / (min(ms) * 1e-3) / 1e12
+    ctx.sync(stream)
+    return {"tflops": max(best.values()), "by_variant": best, "launch_flop": flop.value,
+            "how": "nbtc_probe_ffma: 8 CTAs x 256 threads per SM, 16 independent FMA chains per thread, "
+                   "8192 rounds; best of 10 launches per variant (plain FFMA, packed FP32x2 FMA)"}
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -152,10 +198,30 @@ def _oracle_sample(n_texels: int, seed: int = 11) -> dict:
     return {"seconds": dt, "texels": n_texels}
 
 
-def cpu_baseline(n_texels: int = 1 << 22) -> dict:
+FORM_ERROR_ROWS = (0, 4096, 16)   # rows 0, 16, ..., 4080 of the 4096^2 form workload: 1,048,576 texels
+
+
+def _oracle_form_reference(path: str) -> None:
+    """FP64 oracle outputs of the precision-form workload (4096^2, 12-64-64-64-9)
+    on the error-sample rows, saved for the forms' per-channel error report."""
+    import oracle
+    wl = synth.decode_workload(2)
+    tex = [oracle.decode.level_rgb(lv) for lv in wl.material.levels]
+    rows = np.arange(*FORM_ERROR_ROWS)
+    idx = (rows[:, None] * 4096 + np.arange(4096)[None, :]).reshape(-1)
+    ref = np.concatenate([oracle.decode.decode_grid(wl.material, 4096, 4096, idx[c:c + (1 << 16)], tex=tex)
+                          for c in range(0, len(idx), 1 << 16)])
+    np.save(path, ref)
+
+
+def cpu_baseline(n_texels: int = 1 << 22, form_ref: str | None = None) -> dict:
+    """The oracle leg: times the FP64 oracle on a bounded sample of the headline
+    workload and, untimed, writes its FP64 outputs for the forms' error sample."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
             "print(json.dumps(bench._oracle_sample(%d)))" % (ROOT, n_texels))
+    if form_ref:
+        code += "; bench._oracle_form_reference(%r)" % form_ref
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
     r = json.loads(out.stdout.strip().splitlines()[-1])
     gts = r["texels"] / r["seconds"] / 1e9
@@ -214,10 +280,20 @@ def _time_steps(step, steps: int, warmup: int, flush, stream) -> list:
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def run_forms(args, nb, ctx, stream, flush, peaks, sm_count) -> dict:
+# executed tensor-core FLOP per texel of the 12-64-64-64-9 forms (padded shapes,
+# bias products, three products per layer in the split forms)
+MMA_FLOP = {"fp16_tc": 2 * (16 * 64 + 2 * (16 * 64 + 64 * 64) + 16 * 16 + 64 * 16),
+            "fp8_tc": 2 * (32 * 64 + 2 * 64 * 64 + 64 * 16),
+            "fp16_split_tc": 2 * (3 * 16 * 64 + 2 * (16 * 64 + 3 * 64 * 64) + 16 * 16 + 3 * 64 * 16),
+            "fp8_split_tc": 2 * (2 * 32 * 64 + 2 * 3 * 64 * 64 + 3 * 64 * 16)}
+BOUNDS = {"fp16_tc": 2e-3, "fp8_tc": 2e-2, "fp16_split_tc": 2e-3, "fp8_split_tc": 2e-2}
+
+
+def run_forms(args, nb, ctx, stream, flush, peaks, sm_count, ffma, form_ref) -> dict:
     """Precision forms on the 4096^2, 12-64-64-64-9 workload: FP32 SIMT, FP16 and
-    FP8 E4M3 on tcgen05.  Error = per-channel max |form - FP32 form| over the whole
-    texture (the FP32 form is within 1e-5 of the FP64 oracle in the parity tests)."""
+    FP8 E4M3 on tcgen05, single-rounding and split operands.  Error = per-channel
+    max |form - FP64 oracle| over 1,048,576 texels (every 16th row), against the
+    bound of the form's precision (FP16 2e-3, FP8 2e-2)."""
     import torch
     wl = synth.decode_workload(2)
     mat = nb.Material.from_synth(wl.material)
@@ -226,30 +302,78 @@ def run_forms(args, nb, ctx, stream, flush, peaks, sm_count) -> dict:
     flop = 2 * (12 * 64 + 64 * 64 * 2 + 64 * 9)  # 19,072 per texel
     out32 = torch.empty((n, 9), dtype=torch.float32, device="cuda")
     out16 = torch.empty((n, 9), dtype=torch.float16, device="cuda")
-    res = {"workload": f"decode-{W}sq-bc1x4-mlp12-64-64-64-9", "flop_per_texel": flop}
+    ref = None
+    if form_ref is not None and W == 4096:
+        ref = torch.from_numpy(np.load(form_ref)).cuda()
+    rows = torch.arange(*FORM_ERROR_ROWS, device="cuda")
+
+    def fp64_error(out):
+        if ref is None:
+            return None
+        got = out.view(H, W, 9)[rows].reshape(-1, 9).double()
+        return (got - ref).abs().amax(dim=0).tolist()
+
+    res = {"workload": f"decode-{W}sq-bc1x4-mlp12-64-64-64-9", "flop_per_texel": flop,
+           "error_sample": "1,048,576 texels (rows 0, 16, ..., 4080) against the FP64 oracle"}
     t32 = _time_steps(lambda: nb.decode(ctx, mat, nb.FP32, grid=(W, H), out=out32, stream=stream),
                       max(3, args.steps // 4), 2, flush, stream)
     ms = statistics.mean(t32)
-    res["fp32"] = {"gtexel_s": n / ms / 1e6, "kernel_ms": ms}
-    packed16 = nb.pack_mlp(ctx, mat, nb.FP16, stream=stream)
+    e32 = fp64_error(out32)
+    ach = flop * n / (ms * 1e-3) / 1e12
+    res["fp32"] = {"gtexel_s": n / ms / 1e6, "kernel_ms": ms, "max_abs_err_vs_fp64_per_channel": e32,
+                   "bound": 1e-5, "within_bound": None if e32 is None else max(e32) <= 1e-5,
+                   "roofline": {"bound": "alu", "achieved": ach, "peak": ffma["tflops"], "unit": "TFLOP/s",
+                                "frac": ach / ffma["tflops"], "peak_source": "measured FFMA probe"}}
     absmax = nb.fp8_calibrate(ctx, mat, W, H, 16, stream=stream)
-    packed8 = nb.pack_mlp(ctx, mat, nb.FP8_E4M3, act_absmax=absmax, stream=stream)
+    packed = {"fp16_tc": nb.pack_mlp(ctx, mat, nb.FP16, stream=stream),
+              "fp8_tc": nb.pack_mlp(ctx, mat, nb.FP8_E4M3, act_absmax=absmax, stream=stream),
+              "fp16_split_tc": nb.pack_mlp(ctx, mat, nb.FP16_SPLIT, stream=stream),
+              "fp8_split_tc": nb.pack_mlp(ctx, mat, nb.FP8_E4M3_SPLIT, act_absmax=absmax, stream=stream)}
+    codes = {"fp16_tc": nb.FP16, "fp8_tc": nb.FP8_E4M3, "fp16_split_tc": nb.FP16_SPLIT,
+             "fp8_split_tc": nb.FP8_E4M3_SPLIT}
     bf16 = peaks.get("bf16_tflops", 1900.0)
-    for name, prec, packed, peak in (("fp16_tc", nb.FP16, packed16, bf16), ("fp8_tc", nb.FP8_E4M3, packed8, 2 * bf16)):
-        t = _time_steps(lambda: nb.decode(ctx, mat, prec, packed, grid=(W, H), out=out16, stream=stream),
+    for name in ("fp16_tc", "fp8_tc", "fp16_split_tc", "fp8_split_tc"):
+        prec, pk = codes[name], packed[name]
+        fp8 = "fp8" in name
+        peak = 2 * bf16 if fp8 else bf16
+        t = _time_steps(lambda: nb.decode(ctx, mat, prec, pk, grid=(W, H), out=out16, stream=stream),
                         args.steps, args.warmup, flush, stream)
         ms = statistics.mean(t)
-        err = (out16.float() - out32).abs().amax(dim=0).tolist()
+        err = fp64_error(out16)
         ach = flop * n / (ms * 1e-3) / 1e12
-        algo = n * mat.n_out * 2 + sum(b.numel() * 8 for b in mat.blocks) + packed.numel() * packed.element_size()
-        res[name] = {"gtexel_s": n / ms / 1e6, "kernel_ms": ms, "max_abs_dev_vs_fp32_per_channel": err,
+        exe = MMA_FLOP[name] * n / (ms * 1e-3) / 1e12
+        algo = n * mat.n_out * 2 + sum(b.numel() * 8 for b in mat.blocks) + pk.numel() * pk.element_size()
+        prof = {"fp16_tc": "k_decode_tc_fp16_4096sq", "fp8_tc": "k_decode_tc_fp8_4096sq",
+                "fp16_split_tc": "k_decode_tc_fp16split_4096sq", "fp8_split_tc": "k_decode_tc_fp8split_4096sq"}[name]
+        res[name] = {"gtexel_s": n / ms / 1e6, "kernel_ms": ms, "max_abs_err_vs_fp64_per_channel": err,
+                     "bound": BOUNDS[name], "within_bound": None if err is None else max(err) <= BOUNDS[name],
+                     "speedup_vs_fp32": ms and res["fp32"]["kernel_ms"] / ms,
                      "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": ach / peak, "traffic": _profiled_traffic(f"k_decode_tc_{name.split('_')[0]}_{W}sq"),
-                                  "peak_source": "measured bf16 dense burst" + (" x 2 (fp8 nominal ratio)" if prec == nb.FP8_E4M3 else ""),
+                                  "frac": ach / peak, "traffic": _profiled_traffic(prof),
+                                  "peak_source": "measured bf16 dense burst" + (" x 2 (fp8 nominal ratio)" if fp8 else ""),
+                                  "executed_mma_tflops": exe, "executed_frac": exe / peak,
+                                  "executed_mma_flop_per_texel": MMA_FLOP[name],
                                   "hbm": _hbm(algo, ms, peaks)}}
-    res["fp16_tc_speedup_vs_fp32"] = res["fp16_tc"]["gtexel_s"] / res["fp32"]["gtexel_s"]
     ctx.sync(stream)
     return res
+
+
+def run_config0(args, nb, ctx, stream, flush, ffma) -> dict:
+    """The 256^2 decode (BC1 levels 64^2..8^2, MLP 12-32-32-9, FP32 form): 65,536
+    texels, a few microseconds -- launch- and latency-bound, reported as measured."""
+    import torch
+    wl = synth.decode_workload(0)
+    mat = nb.Material.from_synth(wl.material)
+    n = 256 * 256
+    out = torch.empty((n, 9), dtype=torch.float32, device="cuda")
+    t = _time_steps(lambda: nb.decode(ctx, mat, nb.FP32, grid=(256, 256), out=out, stream=stream),
+                    args.steps, args.warmup, flush, stream)
+    ms = statistics.mean(t)
+    flop = 2 * (12 * 32 + 32 * 32 + 32 * 9) * n
+    ctx.sync(stream)
+    return {"workload": "decode-256sq-bc1x4-mlp12-32-32-9-fp32", "texels": n, "gtexel_s": n / ms / 1e6,
+            "kernel_ms": ms, "alu_frac": flop / (ms * 1e-3) / 1e12 / ffma["tflops"],
+            "note": "too small to fill the GPU: one partial wave of CTAs"}
 
 
 def run_dsweep(args, nb, ctx, stream, flush) -> dict:
@@ -279,7 +403,7 @@ def run_dsweep(args, nb, ctx, stream, flush) -> dict:
     return res
 
 
-def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
+def run_train(args, nb, ctx, stream, flush, sm_count, peaks, ffma) -> dict:
     """One optimisation step on continuous latents (latents 1024^2..128^2, target
     2048^2 x 9, batch 2^20 uniform uv, MLP 12-64-64-9, MSE, Adam): forward, loss,
     backward into MLP and every latent texel, compensated reduction, Adam."""
@@ -295,13 +419,29 @@ def run_train(args, nb, ctx, stream, flush, sm_count, peaks) -> dict:
                     max(3, args.steps // 2), args.warmup, flush, stream)
     ms = statistics.mean(t)
     flop = 32640 * wl.batch
-    peak = _fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    peak = ffma["tflops"]
+    ctx.sync(stream)
+    # the step's L2-atomic co-bound: its latent-gradient scatter alone (same
+    # atomics, same addresses), timed the same way
+    import ctypes
+
+    from paper_2506_06040_gb300._abi import check
+    a = model.args(uvs[0], tgt)
+    scatter = lambda: check(ctx.lib.nbtc_probe_scatter(ctx.handle, ctypes.byref(a), ctypes.c_void_p(stream.cuda_stream)))
+    ts = _time_steps(scatter, max(3, args.steps // 2), args.warmup, flush, stream)
+    ms_sc = statistics.mean(ts)
+    n_atomics = wl.batch * 16
     ctx.sync(stream)
     res = {"workload": wl.name, "steps_per_s": 1e3 / ms, "samples_per_s": wl.batch * 1e3 / ms, "ms_per_step": ms,
            "kernels_per_step": 5, "layout": "latents [h][w][4], target [h][w][12] (padding channels unused)",
            "roofline": {"bound": "alu", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                        "frac": flop / (ms * 1e-3) / 1e12 / peak,
-                        "note": "whole step (forward, backward, reduction, Adam) against the FP32 FFMA peak"}}
+                        "frac": flop / (ms * 1e-3) / 1e12 / peak, "traffic": _profiled_traffic("k_train_batch2p20"),
+                        "peak_source": "measured FFMA probe",
+                        "note": "whole step (forward, backward, reduction, Adam) against the FP32 FFMA peak"},
+           "l2_atomics": {"vector_atomics_per_step": n_atomics, "scatter_alone_ms": ms_sc,
+                          "share_of_step": ms_sc / ms, "atomics_per_s": n_atomics / (ms_sc * 1e-3),
+                          "note": "nbtc_probe_scatter: the step's 16 latent-gradient vector atomics per sample at the "
+                                  "step's addresses, nothing else (the co-bound next to the ALU fraction)"}}
     # the same step on quantisation-aware BC1 latents (raw endpoints + blend factors
     # per level, N(0, 1)): decode, step, straight-through backward, Adam on the raw
     # parameters
@@ -363,7 +503,7 @@ def run_batch(args, nb, ctx, stream, flush) -> dict:
             "frame_lit_ms": statistics.mean(tl), "frame_lit_gpx_s": pixels / statistics.mean(tl) / 1e6}
 
 
-def run_ours(args) -> dict | None:
+def run_ours(args, form_ref=None) -> dict | None:
     import torch
 
     import paper_2506_06040_gb300 as nb
@@ -426,7 +566,7 @@ def run_ours(args) -> dict | None:
     h2d = sum(b.numel() * 8 for b in host_blocks) + host_w.numel() * 4 + host_b.numel() * 4
     d2h = host_out.numel() * 4
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e_steps = max(2, min(args.steps, 5))
+    e_steps = args.steps
     _barrier(world)
     torch.cuda.synchronize()
     copy_stream = torch.cuda.Stream()
@@ -444,7 +584,9 @@ def run_ours(args) -> dict | None:
     e2e = _job_rate(n, e2e_ms, world)
 
     flop = FLOP_PER_TEXEL_C1 * n
-    peak_tf = _fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    ffma = measure_ffma_peak(nb, ctx, stream, sm_count)
+    ffma["unit_count_tflops"] = _fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    peak_tf = ffma["tflops"]
     achieved_tf = flop / (kernel_ms * 1e-3) / 1e12
     res = {
         "metric": METRIC, "value": value, "unit": "Gtexel/s", "n_gpus": world, "steps": args.steps,
@@ -453,7 +595,7 @@ def run_ours(args) -> dict | None:
         "config": _config(world, n),
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_tf, "traffic": _profiled_traffic("k_decode_fp32_wide_4096sq"),
-                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
+                     "peak_source": "measured: the library's FFMA probe kernel (see ffma_peak)",
                      "kernel": "k_decode_fp32_wide<2, 2>", "kernel_ms": kernel_ms,
                      "hbm": _hbm(n * 9 * 4 + sum(b.numel() * 8 for b in mat.blocks) +
                                  (mat.weights.numel() + mat.biases.numel()) * 4, kernel_ms, peaks)},
@@ -461,13 +603,15 @@ def run_ours(args) -> dict | None:
         "gpu_launches": args.steps,
         "clocks": clk,
         "wall_s_timed": wall,
+        "ffma_peak": ffma,
     }
+    res["config0"] = run_config0(args, nb, ctx, stream, flush, ffma)
     if "forms" in args.parts:
-        res["forms"] = run_forms(args, nb, ctx, stream, flush, peaks, sm_count)
+        res["forms"] = run_forms(args, nb, ctx, stream, flush, peaks, sm_count, ffma, form_ref)
     if "dsweep" in args.parts:
         res["dsweep"] = run_dsweep(args, nb, ctx, stream, flush)
     if "train" in args.parts:
-        res["train"] = run_train(args, nb, ctx, stream, flush, sm_count, peaks)
+        res["train"] = run_train(args, nb, ctx, stream, flush, sm_count, peaks, ffma)
     if "batch" in args.parts:
         res["batch"] = run_batch(args, nb, ctx, stream, flush)
     ctx.close()
@@ -553,10 +697,16 @@ def main():
         res = run_reference(args)
     else:
         rank, world, _ = _dist()
-        cpu = None
+        cpu, form_ref = None, None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline()  # before the first GPU call (fresh process, spawn-safe)
-        res = run_ours(args)
+            if "forms" in args.parts and args.form_side == 4096:
+                form_ref = tempfile.mktemp(suffix=".npy")
+            cpu = cpu_baseline(form_ref=form_ref)  # before the first GPU call (fresh process, spawn-safe)
+        try:
+            res = run_ours(args, form_ref)
+        finally:
+            if form_ref and os.path.exists(form_ref):
+                os.unlink(form_ref)
         if res is not None:
             res["cpu_baseline"] = cpu
     if res is not None:

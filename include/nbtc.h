@@ -438,6 +438,30 @@ nbtc_status nbtc_batch_info_get(nbtc_batch* plan, nbtc_batch_info* info);
 /* Frees the plan (synchronises its device first). */
 nbtc_status nbtc_batch_destroy(nbtc_batch* plan);
 
+/* ------------------------------------------------------------------ measurement probes
+ *
+ * Kernels with a known amount of work, for the measured ceilings the decode and
+ * training kernels are reported against (no counterpart in the paper).  Each
+ * enqueues one launch on `stream`; the caller times it (CUDA events). */
+
+/* FP32 FFMA throughput: `ctas` CTAs of 256 threads, each running `iters`
+ * rounds of 16 independent fused multiply-adds (8 packed FP32x2 FMAs when
+ * `packed` is nonzero).  *flop receives the launch's FLOP count,
+ * ctas * 256 * iters * 32.  out_dev: 4 bytes of device memory the kernel may
+ * write (it keeps the arithmetic live; nothing is stored in practice).
+ * NBTC_ERR_INVALID_ARG for ctas < 1, iters < 1, NULL or non-device pointers. */
+nbtc_status nbtc_probe_ffma(nbtc_context* ctx, int32_t ctas, int32_t iters, int32_t packed, float* out_dev,
+                            double* flop, void* stream);
+
+/* The latent-gradient scatter of nbtc_train_step alone: for each of
+ * args->batch samples at args->uv, the four bilinear taps of every latent level
+ * receive the same atomic adds the step makes (one 16-byte vector add per tap
+ * with latent_stride 4, else three 4-byte adds) of a constant, into
+ * args->latent_grads -- the step's L2 atomics at the step's addresses, with no
+ * other work.  It adds to latent_grads (caller-owned; zero them or discard).
+ * Argument rules as nbtc_train_step (target, moments and workspace unused). */
+nbtc_status nbtc_probe_scatter(nbtc_context* ctx, const nbtc_train_args* args, void* stream);
+
 /* Allocation-free training step (the paper has no counterpart: this is an
  * integration convenience).  For callers that may not allocate device memory
  * at all -- engines that sub-allocate a budget reserved up front, plugin hosts
@@ -445,13 +469,18 @@ nbtc_status nbtc_batch_destroy(nbtc_batch* plan);
  * afford the device synchronisation cudaMalloc / cudaFree can cause -- and so
  * can neither supply args->workspace nor create an nbtc_context.  Same work and
  * results as nbtc_train_step, on the current CUDA device; args->workspace is
- * ignored.  Its scratch is a fixed 7.72 MB device array inside the library
- * (room for one CTA per SM on devices with up to 160 SMs; larger devices get
- * NBTC_ERR_UNSUPPORTED), held by every GPU that loads the library until the
- * process exits.  The first call on a device looks up that array's device
- * address (make that first call before any stream capture).  All calls share
- * the array: calls that overlap on the GPU race and must be ordered by the
- * caller.  Nothing is allocated by this call. */
+ * ignored.  Its scratch is a fixed 7.72 MB device array inside the library,
+ * held by every GPU that loads the library until the process exits: room for
+ * the partial sums of at most 160 CTAs (one per SM, so a batch that needs
+ * more than 160 CTAs, possible only on a device with more than 160 SMs, gets
+ * NBTC_ERR_UNSUPPORTED) and, when a small batch leaves room after them, for
+ * its per-sample gather records (the step then gathers first, as
+ * nbtc_train_step does; otherwise it gathers inside its main kernel -- same
+ * results either way).  The first call on a device looks up that array's
+ * device address and keeps it for the process (make that first call before
+ * any stream capture; a cudaDeviceReset after it is not supported).  All
+ * calls share the array: calls that overlap on the GPU race and must be
+ * ordered by the caller.  Nothing is allocated by this call. */
 nbtc_status nbtc_train_step_noalloc(const nbtc_train_args* args, float* loss_dev, void* stream);
 
 #ifdef __cplusplus

@@ -7,7 +7,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_float, c_int, c_int32, c_int64, c_size_t, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int32, c_int64, c_size_t, c_void_p
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnbtc.so")
@@ -104,6 +104,8 @@ PROTOTYPES = {
     "nbtc_render_frame": (c_int, [c_void_p, c_void_p, c_void_p]),
     "nbtc_batch_info_get": (c_int, [c_void_p, POINTER(BatchInfo)]),
     "nbtc_batch_destroy": (c_int, [c_void_p]),
+    "nbtc_probe_ffma": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, POINTER(c_double), c_void_p]),
+    "nbtc_probe_scatter": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p]),
 }
 
 _lib = None

@@ -43,8 +43,15 @@ PtrKind ptr_kind(const void* p) {
     cudaGetLastError();
     return kPtrOther;
   }
-  if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) return kPtrDevice;
-  if (pa.type == cudaMemoryTypeHost && pa.devicePointer) return kPtrPinned;
+  if (pa.type == cudaMemoryTypeManaged) return kPtrDevice;
+  if (pa.type == cudaMemoryTypeDevice) {
+    // device memory of another GPU is not this launch's to read
+    int dev = -1;
+    return cudaGetDevice(&dev) == cudaSuccess && pa.device == dev ? kPtrDevice : kPtrOther;
+  }
+  // pinned host memory that the kernels reach at its own address (the kernels
+  // take the caller's pointer as is; a registration mapped elsewhere is refused)
+  if (pa.type == cudaMemoryTypeHost && pa.devicePointer == p) return kPtrPinned;
   return kPtrOther;
 }
 

@@ -716,6 +716,38 @@ nbtc_status launch_adam(nbtc_context* ctx, const nbtc_train_args* A, float lr, c
   return cuda_check(cudaGetLastError(), "launch k_adam_latent");
 }
 
+// The latent-gradient scatter of a training step alone: per sample, the four
+// bilinear taps of every level receive the atomic adds k_train makes (16-byte
+// vector adds with 4-float texels), of a constant gradient, with no other work.
+// Timed by the caller, it measures the step's L2-atomic co-bound.
+template <bool LV>
+__global__ void __launch_bounds__(256) k_scatter_probe(TrainDev a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.batch) return;
+  const float2 uv = __ldg(reinterpret_cast<const float2*>(a.uv) + i);
+  const float g = 1e-3f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
+    float* G = a.lgrad[k];
+    if constexpr (LV) {
+      float4* G4 = reinterpret_cast<float4*>(G);
+      atomicAdd(G4 + T.i00, make_float4(T.w00 * g, T.w00 * g, T.w00 * g, 0.f));
+      atomicAdd(G4 + T.i10, make_float4(T.w10 * g, T.w10 * g, T.w10 * g, 0.f));
+      atomicAdd(G4 + T.i01, make_float4(T.w01 * g, T.w01 * g, T.w01 * g, 0.f));
+      atomicAdd(G4 + T.i11, make_float4(T.w11 * g, T.w11 * g, T.w11 * g, 0.f));
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        atomicAdd(G + 3 * T.i00 + c, T.w00 * g);
+        atomicAdd(G + 3 * T.i10 + c, T.w10 * g);
+        atomicAdd(G + 3 * T.i01 + c, T.w01 * g);
+        atomicAdd(G + 3 * T.i11 + c, T.w11 * g);
+      }
+    }
+  }
+}
+
 static nbtc_status check_train(const nbtc_train_args* A, bool need_target, bool need_adam, bool need_latent_adam) {
   if (!A) return fail(NBTC_ERR_INVALID_ARG, "train args NULL");
   if (A->num_levels != 4) return fail(NBTC_ERR_UNSUPPORTED, "training takes 4 latent levels");
@@ -748,7 +780,8 @@ static nbtc_status check_train(const nbtc_train_args* A, bool need_target, bool 
   // pointer kinds: every buffer the kernels touch is device memory or pinned host memory
   nbtc_status pk;
   for (int k = 0; k < 4; ++k) {
-    if ((pk = need_readable(A->latents[k], "latents")) || (pk = need_readable(A->latent_grads[k], "latent_grads")))
+    // the gradients take atomic adds: device memory only
+    if ((pk = need_readable(A->latents[k], "latents")) || (pk = need_device(A->latent_grads[k], "latent_grads")))
       return pk;
     if (need_latent_adam &&
         ((pk = need_readable(A->latent_m[k], "latent_m")) || (pk = need_readable(A->latent_v[k], "latent_v"))))
@@ -886,11 +919,15 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
   if (mode == kModeFwd) {
     if (A->batch == 0) return NBTC_OK;
     if (!y) return fail(NBTC_ERR_INVALID_ARG, "y is NULL");
+    if ((st = need_readable(y, "y"))) return st;
     d.y = y;
     return launch_train_kernel<kModeFwd>(A, d, grid, s);
   }
   if (!workspace || !aligned(workspace, 16) || workspace_bytes < (size_t)grid * kPart * sizeof(float))
     return fail(NBTC_ERR_INVALID_ARG, "workspace NULL, misaligned or too small");
+  if ((st = need_device(workspace, "workspace"))) return st;
+  if (loss && (st = need_readable(loss, "loss"))) return st;
+  if (mode == kModeBwd && dy && (st = need_readable(dy, "dy"))) return st;
   if ((st = zero_latent_grads(ctx, A, s))) return st;
   if ((st = pre_gather(ctx, A, d, grid, mode == kModeTrain, workspace, workspace_bytes, s))) return st;
   if (mode == kModeBwd) {
@@ -991,4 +1028,20 @@ extern "C" nbtc_status nbtc_train_step_noalloc(const nbtc_train_args* args, floa
                                           " SMs; its fixed scratch holds partial sums for at most 160");
   return train_step_impl(&local, args, loss_dev, (cudaStream_t)stream, 2, nullptr, nullptr, scratch,
                          sizeof(g_noalloc_partials));
+}
+
+extern "C" nbtc_status nbtc_probe_scatter(nbtc_context* ctx, const nbtc_train_args* args, void* stream) {
+  NBTC_RANGE();
+  using namespace nbtc;
+  nbtc_status st;
+  if ((st = enter(ctx))) return st;
+  if ((st = check_train(args, false, false, false))) return st;
+  if (args->batch == 0) return NBTC_OK;
+  const TrainDev d = make_dev(args, nullptr);
+  const unsigned grid = (unsigned)((args->batch + 255) / 256);
+  if (latent_stride(args) == 4)
+    k_scatter_probe<true><<<grid, 256, 0, (cudaStream_t)stream>>>(d);
+  else
+    k_scatter_probe<false><<<grid, 256, 0, (cudaStream_t)stream>>>(d);
+  return cuda_check(cudaGetLastError(), "launch k_scatter_probe");
 }

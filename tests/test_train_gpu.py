@@ -208,7 +208,33 @@ def test_invalid_strides(nb, ctx):
     assert run(lambda a: setattr(a, "target", tgt_host.data_ptr())) == _abi.ERR_INVALID_ARG
     uv_host = uv.cpu()
     assert run(lambda a: setattr(a, "uv", uv_host.data_ptr())) == _abi.ERR_INVALID_ARG
+    # the workspace must be device memory; the loss device or pinned host memory;
+    # latent gradients (atomic adds) device memory, also when the host's are pinned
+    ws_host = torch.empty(64 << 20, dtype=torch.uint8)
+    assert run(lambda a: setattr(a, "workspace", ws_host.data_ptr())) == _abi.ERR_INVALID_ARG
+    ws_pinned = torch.empty(64 << 20, dtype=torch.uint8).pin_memory()
+    assert run(lambda a: setattr(a, "workspace", ws_pinned.data_ptr())) == _abi.ERR_INVALID_ARG
+    g_pinned = torch.zeros(model.latent_grads[2].numel(), dtype=torch.float32).pin_memory()
+    assert run(lambda a: a.latent_grads.__setitem__(2, g_pinned.data_ptr())) == _abi.ERR_INVALID_ARG
+    a = model.args(uv, tgt)
+    model._workspace(ctx, a)
+    loss_host = torch.empty(1)
+    assert ctx.lib.nbtc_train_step(ctx.handle, ctypes.byref(a), ctypes.c_void_p(loss_host.data_ptr()),
+                                   s) == _abi.ERR_INVALID_ARG
+    y_host = torch.empty((uv.shape[0], 9))
+    assert ctx.lib.nbtc_forward_continuous(ctx.handle, ctypes.byref(a), ctypes.c_void_p(y_host.data_ptr()),
+                                           s) == _abi.ERR_INVALID_ARG
+    dy_host = torch.zeros((uv.shape[0], 9))
+    assert ctx.lib.nbtc_backward_continuous(ctx.handle, ctypes.byref(a), ctypes.c_void_p(dy_host.data_ptr()),
+                                            s) == _abi.ERR_INVALID_ARG
+    # a pinned host loss is written over the host link
+    loss_pinned = torch.zeros(1).pin_memory()
+    a = model.args(uv, tgt)
+    model._workspace(ctx, a)
+    assert ctx.lib.nbtc_train_step(ctx.handle, ctypes.byref(a), ctypes.c_void_p(loss_pinned.data_ptr()),
+                                   s) == _abi.OK
     ctx.sync()
+    assert float(loss_pinned[0]) > 0
 
 
 def test_layouts_give_the_same_step(nb, ctx):

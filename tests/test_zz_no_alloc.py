@@ -25,7 +25,11 @@ def _rel_ok(got, ref):
     return np.linalg.norm(got - ref) <= REL * nrm and np.abs(got - ref).max() <= REL * np.abs(ref).max()
 
 
-def test_no_alloc_step_matches_workspace_step_twice():
+@pytest.mark.parametrize("batch", [3000 + 7, 30000 + 11])
+def test_no_alloc_step_matches_workspace_step_twice(batch):
+    """batch 3,007: partial sums and gather records both fit the fixed array (the
+    step gathers first); batch 30,011: only the partial sums fit (the step
+    gathers inside its main kernel)."""
     require_gpu()
     import paper_2506_06040_gb300 as nb
     from paper_2506_06040_gb300 import _abi
@@ -36,7 +40,7 @@ def test_no_alloc_step_matches_workspace_step_twice():
     lat = [rng.normal(s * s * 3, 0.1).reshape(s, s, 3).astype(np.float32) for s in sides]
     mlp = synth.he_mlp(synth.Rng(91, 2), [12, 64, 64, 9])
     target = synth.sinusoid_target(synth.Rng(91, 3), 256)
-    wl = synth.TrainWorkload("no-alloc", sides, synth.SHIFTS, lat, mlp, target, 30000 + 11, 91)
+    wl = synth.TrainWorkload("no-alloc", sides, synth.SHIFTS, lat, mlp, target, batch, 91)
 
     ctx = nb.Context(0)
     lib = _abi.load()
