@@ -49,7 +49,7 @@ typedef enum {
   NBTC_ERR_UNSUPPORTED = 2, /* valid request the library has no kernel for */
   NBTC_ERR_CUDA = 3,        /* a CUDA runtime call failed                    */
   NBTC_ERR_TIMEOUT = 4,     /* a device-side bounded wait expired            */
-  NBTC_ERR_BOUNDS = 5       /* reserved (no build of this library reports it) */
+  NBTC_ERR_BOUNDS = 5       /* checked build: a gather index outside its array */
 } nbtc_status;
 
 /* Precision forms of the decode (Sec. 4 runs the MLP on matrix units in low
@@ -147,6 +147,18 @@ const char* nbtc_last_error(void);
  * bulk copies have finished; the context stays usable.  Waits that guard
  * resources (weight loads, the final drain) always use the fixed budget. */
 nbtc_status nbtc_set_wait_budget(nbtc_context* ctx, int64_t spins);
+
+/* Checked build.  libnbtc_checked.so is this library compiled with
+ * NBTC_CHECKED: every gather index its kernels form (BC1 blocks of every level
+ * and mip, latent and target taps of the training kernels, frame pixels and
+ * the binning's list slots) is tested against the extent of the array it
+ * indexes; an index outside it records NBTC_ERR_BOUNDS in the context's status
+ * word (reported by nbtc_status_sync) and is replaced by 0, so no access leaves
+ * its array and nothing traps.  Results are otherwise those of libnbtc.so.
+ * Tests only: nbtc_set_check_plant adds `offset` to every such index of this
+ * context's later calls (0 restores), so the checks can be seen to fire; the
+ * default build returns NBTC_ERR_UNSUPPORTED. */
+nbtc_status nbtc_set_check_plant(nbtc_context* ctx, int32_t offset);
 
 /* ------------------------------------------------------------------ decode */
 

@@ -11,6 +11,8 @@ from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int32, c_int64
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnbtc.so")
+# the same library built with per-access bounds checks (NBTC_CHECKED)
+LIB_CHECKED_PATH = os.path.join(HERE, "libnbtc_checked.so")
 
 MAX_LEVELS, MAX_LAYERS, MAX_MIPS = 8, 4, 16
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_BOUNDS = range(6)
@@ -106,9 +108,11 @@ PROTOTYPES = {
     "nbtc_batch_destroy": (c_int, [c_void_p]),
     "nbtc_probe_ffma": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, POINTER(c_double), c_void_p]),
     "nbtc_probe_scatter": (c_int, [c_void_p, POINTER(TrainArgs), c_void_p]),
+    "nbtc_set_check_plant": (c_int, [c_void_p, c_int32]),
 }
 
 _lib = None
+_lib_checked = None
 
 
 class NbtcError(RuntimeError):
@@ -117,21 +121,32 @@ class NbtcError(RuntimeError):
         self.code = code
 
 
-def load() -> ctypes.CDLL:
-    """Loads libnbtc.so (raises if it is missing: there is no fallback path)."""
-    global _lib
+def _open(path: str) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in PROTOTYPES.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+def load(checked: bool = False) -> ctypes.CDLL:
+    """Loads libnbtc.so, or with checked=True its bounds-checked build
+    libnbtc_checked.so (raises if it is missing: there is no fallback path)."""
+    global _lib, _lib_checked
+    if checked:
+        if _lib_checked is None:
+            _lib_checked = _open(LIB_CHECKED_PATH)
+        return _lib_checked
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
-        lib = ctypes.CDLL(LIB_PATH)
-        for name, (res, args) in PROTOTYPES.items():
-            f = getattr(lib, name)
-            f.restype, f.argtypes = res, args
-        _lib = lib
+        _lib = _open(LIB_PATH)
     return _lib
 
 
 def check(code: int) -> None:
     if code != OK:
         msg = load().nbtc_last_error().decode(errors="replace")
+        if not msg and _lib_checked is not None:
+            msg = _lib_checked.nbtc_last_error().decode(errors="replace")
         raise NbtcError(code, msg)

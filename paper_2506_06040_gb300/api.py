@@ -21,10 +21,13 @@ def _ptr(t) -> c_void_p:
 
 
 class Context:
-    """A library context on one CUDA device (owns the device status word)."""
+    """A library context on one CUDA device (owns the device status word).
+    checked=True runs every call of this context through the bounds-checked
+    build of the library (libnbtc_checked.so)."""
 
-    def __init__(self, device: int = 0):
-        self.lib = _abi.load()
+    def __init__(self, device: int = 0, checked: bool = False):
+        self.lib = _abi.load(checked)
+        self.checked = checked
         self.device = device
         h = c_void_p()
         check(self.lib.nbtc_create(device, byref(h)))
@@ -50,6 +53,11 @@ class Context:
 
     def set_wait_budget(self, spins: int):
         check(self.lib.nbtc_set_wait_budget(self.handle, spins))
+
+    def set_check_plant(self, offset: int):
+        """Checked build, tests only: offset added to every gather index, so that
+        the bounds checks fire (NBTC_ERR_UNSUPPORTED in the default build)."""
+        check(self.lib.nbtc_set_check_plant(self.handle, offset))
 
 
 class Material:

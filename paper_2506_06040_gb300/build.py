@@ -1,8 +1,13 @@
-"""Builds the in-tree CUDA library `libnbtc.so` for sm_103a with nvcc.
+"""Builds the in-tree CUDA library `libnbtc.so` for sm_103a with nvcc, and its
+checked twin `libnbtc_checked.so` (the same sources compiled with NBTC_CHECKED:
+every gather index of the kernels is tested against its array's extent, and an
+index outside it records NBTC_ERR_BOUNDS in the status word instead of being
+used).
 
-Each `csrc/*.cu` compiles to an object under `_build/` in parallel (rebuilt
-when it or any header is newer), then nvcc links them into the shared library
-next to this file, with the CUDA runtime linked statically.
+Each `csrc/*.cu` compiles to an object under `_build/` (and `_build/checked/`)
+in one parallel pass (rebuilt when it or any header is newer), then nvcc links
+each set into its shared library next to this file, with the CUDA runtime
+linked statically.
 """
 from __future__ import annotations
 
@@ -15,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnbtc.so")
+LIB_CHECKED = os.path.join(HERE, "libnbtc_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", SRC]
@@ -31,18 +37,23 @@ def _newest_header() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
-def build(verbose: bool = False, extra_flags=None) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose: bool = False, extra_flags=None, checked: bool = True) -> str:
+    """Builds libnbtc.so (and, with checked=True, libnbtc_checked.so); returns
+    the path of libnbtc.so."""
     nvcc = _nvcc()
     srcs = sorted(glob.glob(os.path.join(SRC, "*.cu")))
     hdr_t = _newest_header()
-    flags = FLAGS + list(extra_flags or [])
+    variants = [(OUT_DIR, LIB, [])] + ([(os.path.join(OUT_DIR, "checked"), LIB_CHECKED, ["-DNBTC_CHECKED"])]
+                                       if checked else [])
+    for d, _, _ in variants:
+        os.makedirs(d, exist_ok=True)
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+    def compile_one(job) -> str:
+        src, out_dir, defs = job
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_t) and not extra_flags:
             return obj
-        cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *defs, *list(extra_flags or []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -50,13 +61,16 @@ def build(verbose: bool = False, extra_flags=None) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", LIB, *objs, "-cudart", "static"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
+    jobs = [(src, d, defs) for d, _, defs in variants for src in srcs]
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for i, (_, lib, _) in enumerate(variants):
+        mine = objs[i * len(srcs):(i + 1) * len(srcs)]
+        if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in mine):
+            cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", lib, *mine, "-cudart", "static"]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
     return LIB
 
 

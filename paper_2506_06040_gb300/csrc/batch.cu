@@ -54,6 +54,8 @@ struct FrameDev {
   int chunk_cap;
   int chunk_tiles;
   int* stats;    // [uniform tiles, mixed tiles, packed tiles]
+  int64_t ulist_cap, plist_cap;  // slots of ulist and plist (bounds of the checked build)
+  int* status;                   // context status word (checked build)
 };
 
 // Pixel j (0..127) of screen tile t.
@@ -149,7 +151,9 @@ __global__ void k_frame_bin(FrameDev F) {
     if (lane == 0) {
       const int m = F.tmat[t];
       const int pos = atomicAdd(F.ucur + m, 1);
-      F.ulist[F.uoff[m] + pos] = t;
+      int64_t slot = (int64_t)F.uoff[m] + pos;
+      NBTC_CHECK_INDEX(slot, F.ulist_cap, F.status);
+      F.ulist[slot] = t;
     }
     return;
   }
@@ -165,7 +169,11 @@ __global__ void k_frame_bin(FrameDev F) {
     int base = 0;
     if (id >= 0 && lane == leader) base = atomicAdd(F.pcur + id, __popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (id >= 0) F.plist[(int64_t)F.poff[id] * kTileK + base + __popc(peers & lt)] = px;
+    if (id >= 0) {
+      int64_t slot = (int64_t)F.poff[id] * kTileK + base + __popc(peers & lt);
+      NBTC_CHECK_INDEX(slot, F.plist_cap, F.status);
+      F.plist[slot] = px;
+    }
   }
 }
 
@@ -304,6 +312,7 @@ static nbtc_status enqueue_render(nbtc_context* ctx, nbtc_batch* B, cudaStream_t
   p.light = make_light(B->frame);
   p.fout = static_cast<uint16_t*>(B->frame.out);
   p.frame_w = F.w;
+  p.frame_pixels = (int64_t)F.w * F.h;
   p.tile_w = F.tw;
   p.tile_h = F.th;
   p.tiles_x = F.tiles_x;
@@ -473,6 +482,7 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     MatDev& d = md[m];
     memset(&d, 0, sizeof(d));
     make_level_views(&M.latents, 0, d.d.lv);
+    attach_checks(ctx, d.d.lv, 4);
     d.d.wrap = M.latents.address == NBTC_WRAP;
     d.d.grid_w = M.out ? M.out_w : 0;
     d.d.grid_h = M.out ? M.out_h : 0;
@@ -536,6 +546,9 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
     F.ulist = q; q += max_tiles;
     F.nchunks = q; q += 1;
     F.plist = q;
+    F.ulist_cap = max_tiles;
+    F.plist_cap = (int64_t)B->plist_ints;
+    F.status = ctx->status_dev;
     F.chunk_cap = 2 * (max_tiles + count) + 16;
     NBTC_TRY(cuda_check(cudaMalloc(&B->fchunks, sizeof(WorkChunk) * F.chunk_cap), "frame chunks"));
     NBTC_TRY(cuda_check(cudaMalloc(&B->fcounter, sizeof(int)), "frame counter"));

@@ -19,6 +19,10 @@ struct LevelView {
   int32_t w, h;            // texels
   int32_t wb;              // blocks per row (w / 4)
   float shift;             // texels, both axes
+#ifdef NBTC_CHECKED
+  int* status;             // checked build: where an index outside the level is recorded
+  int32_t plant;           // checked build, tests only: added to every block index (0 otherwise)
+#endif
 };
 
 // ---------------------------------------------------------------- status word
@@ -26,6 +30,36 @@ struct LevelView {
 // First fault wins; later faults leave the recorded code in place.
 __device__ __forceinline__ void record_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------- bounds checks
+//
+// The checked build (compiled with NBTC_CHECKED) tests every gather index the
+// kernels form against the extent of the array it indexes: an index outside
+// it records NBTC_ERR_BOUNDS in the launch's status word and is replaced by 0,
+// a valid element, so no access leaves its array and nothing traps.  The
+// default build compiles the checks away.
+#ifdef NBTC_CHECKED
+__device__ __forceinline__ int64_t checked_index(int64_t i, int64_t n, int* status) {
+  if (i < 0 || i >= n) {
+    record_status(status, NBTC_ERR_BOUNDS);
+    return 0;
+  }
+  return i;
+}
+#define NBTC_CHECK_INDEX(i, n, status) ((i) = ::nbtc::checked_index((i), (n), (status)))
+#else
+#define NBTC_CHECK_INDEX(i, n, status) ((void)0)
+#endif
+
+// Index of block (bx, by) of a level view.
+__device__ __forceinline__ int64_t block_index(const LevelView& L, int bx, int by) {
+  int64_t i = (int64_t)by * L.wb + bx;
+#ifdef NBTC_CHECKED
+  i += L.plant;
+  NBTC_CHECK_INDEX(i, (int64_t)L.wb * (L.h / 4), L.status);
+#endif
+  return i;
 }
 
 // ---------------------------------------------------------------- BC1 decode
@@ -74,7 +108,7 @@ __device__ __forceinline__ uint32_t bc1_texel(uint64_t blk, int tx, int ty) {
 }
 
 __device__ __forceinline__ uint32_t fetch_texel(const LevelView& L, int x, int y) {
-  const uint64_t blk = __ldg(L.blocks + (size_t)(y >> 2) * L.wb + (x >> 2));
+  const uint64_t blk = __ldg(L.blocks + block_index(L, x >> 2, y >> 2));
   return bc1_texel(blk, x & 3, y & 3);
 }
 

@@ -116,8 +116,25 @@ nbtc_status make_level_views(const nbtc_latents* lat, int mip, LevelView* views)
     views[k].h = h;
     views[k].wb = w / 4;
     views[k].shift = L.shift;
+#ifdef NBTC_CHECKED
+    views[k].status = nullptr;
+    views[k].plant = 0;
+#endif
   }
   return NBTC_OK;
+}
+
+void attach_checks(const nbtc_context* ctx, LevelView* views, int n) {
+#ifdef NBTC_CHECKED
+  for (int k = 0; k < n; ++k) {
+    views[k].status = ctx->status_dev;
+    views[k].plant = ctx->check_plant;
+  }
+#else
+  (void)ctx;
+  (void)views;
+  (void)n;
+#endif
 }
 
 }  // namespace nbtc
@@ -195,6 +212,17 @@ const char* nbtc_status_string(nbtc_status s) {
 
 const char* nbtc_last_error(void) { return g_last_error.c_str(); }
 
+nbtc_status nbtc_set_check_plant(nbtc_context* ctx, int32_t offset) {
+  if (!ctx) return fail(NBTC_ERR_INVALID_ARG, "ctx is NULL");
+#ifdef NBTC_CHECKED
+  ctx->check_plant = offset;
+  return NBTC_OK;
+#else
+  (void)offset;
+  return fail(NBTC_ERR_UNSUPPORTED, "bounds checks exist only in the checked build (libnbtc_checked.so)");
+#endif
+}
+
 nbtc_status nbtc_set_wait_budget(nbtc_context* ctx, int64_t spins) {
   if (!ctx) return fail(NBTC_ERR_INVALID_ARG, "context is NULL");
   if (spins < -1) return fail(NBTC_ERR_INVALID_ARG, "spins must be >= -1");
@@ -215,6 +243,7 @@ nbtc_status nbtc_bc1_decode_level(nbtc_context* ctx, const nbtc_level* level, in
   lat.levels[0] = *level;
   LevelView v;
   if ((st = make_level_views(&lat, mip, &v))) return st;
+  attach_checks(ctx, &v, 1);
   if ((st = need_inputs(&lat, nullptr)) || (st = need_readable(out_dev, "out"))) return st;
   return launch_bc1_decode(ctx, v, out_dev, (cudaStream_t)stream);
 }
@@ -230,6 +259,7 @@ static nbtc_status make_decode_args(nbtc_context* ctx, const nbtc_latents* lat, 
   if (mlp->dims[0] != 3 * lat->num_levels)
     return fail(NBTC_ERR_INVALID_ARG, "mlp.dims[0] must be 3 * num_levels");
   if ((st = make_level_views(lat, 0, a.lv))) return st;
+  attach_checks(ctx, a.lv, 4);
   if (n < 0) return fail(NBTC_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return NBTC_OK;  // nothing to decode; no pointer is touched
   if ((st = need_inputs(lat, mlp))) return st;

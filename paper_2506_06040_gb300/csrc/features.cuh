@@ -108,8 +108,8 @@ struct BlockPair {
 __device__ __forceinline__ BlockPair load_column(const DecodeArgs& a, const ColumnJob& J) {
   const LevelView& L = a.lv[J.k];
   BlockPair B;
-  B.b0 = __ldg(L.blocks + (size_t)(J.y0 >> 2) * L.wb + (J.x >> 2));
-  B.b1 = __ldg(L.blocks + (size_t)(J.y1 >> 2) * L.wb + (J.x >> 2));
+  B.b0 = __ldg(L.blocks + block_index(L, J.x >> 2, J.y0 >> 2));
+  B.b1 = __ldg(L.blocks + block_index(L, J.x >> 2, J.y1 >> 2));
   return B;
 }
 
@@ -248,16 +248,15 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
     if (key != C.key) {
       // moving down one latent row, the new pair's upper texel is the old pair's
       // lower one: decode only the new lower texel
-      const uint64_t* col = L.blocks + (C.jx >> 2);
       uint32_t t0;
       if (key == C.key + 1) {
         t0 = C.t1;
       } else {
         const int y0 = wrap_or_clamp(key, L.h, a.wrap);
-        t0 = bc1_texel(__ldg(col + (size_t)(y0 >> 2) * L.wb), C.jx & 3, y0 & 3);
+        t0 = bc1_texel(__ldg(L.blocks + block_index(L, C.jx >> 2, y0 >> 2)), C.jx & 3, y0 & 3);
       }
       const int y1 = wrap_or_clamp(key + 1, L.h, a.wrap);
-      const uint32_t t1 = bc1_texel(__ldg(col + (size_t)(y1 >> 2) * L.wb), C.jx & 3, y1 & 3);
+      const uint32_t t1 = bc1_texel(__ldg(L.blocks + block_index(L, C.jx >> 2, y1 >> 2)), C.jx & 3, y1 & 3);
       C.key = key;
       C.t1 = t1;
 #pragma unroll
@@ -274,7 +273,7 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
     const int keyn = (int)floorf(tyn);
     if (keyn != key && j + 1 < a.grid_h) {
       const int y1 = wrap_or_clamp(keyn + 1, L.h, a.wrap);
-      sm100::prefetch_l1(L.blocks + (C.jx >> 2) + (size_t)(y1 >> 2) * L.wb);
+      sm100::prefetch_l1(L.blocks + block_index(L, C.jx >> 2, y1 >> 2));
     }
   }
   if (C.total > NT) {

@@ -14,6 +14,7 @@ struct nbtc_context {
   long long wait_budget = 0;       // spins per bounded device wait (0 = default, -1 = give up at once)
   int tc_groups = 4;               // warpgroups per CTA of the tensor-core decode (3 or 4)
   int fp32_groups = 2;             // independent thread groups per CTA of the FP32 wide decode (1 or 2)
+  int check_plant = 0;             // checked build, tests only: offset added to gather indices
 };
 
 #include <nvtx3/nvToolsExt.h>
@@ -42,6 +43,10 @@ nbtc_status enter(nbtc_context* ctx);
 // Validates a latent pyramid for the decode kernels and fills the device
 // views of mip `mip` of each level.
 nbtc_status make_level_views(const nbtc_latents* lat, int mip, LevelView* views);
+
+// Checked build: points the views' bounds checks at the context's status word
+// (and its test-only index offset); no-op otherwise.
+void attach_checks(const nbtc_context* ctx, LevelView* views, int n);
 
 // Validates an MLP descriptor (shape and pointers).
 nbtc_status check_mlp(const nbtc_mlp* mlp);

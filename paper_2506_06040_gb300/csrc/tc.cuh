@@ -114,6 +114,7 @@ struct TcArgs {
   LightDev light;          // frame: lighting constants
   uint16_t* fout;          // frame: per-pixel output (nout FP16)
   int frame_w, tile_w, tile_h, tiles_x;
+  int64_t frame_pixels;    // frame: pixel count (bounds of the checked build)
 };
 
 // Per-CTA view of the chunk being decoded (in shared memory).

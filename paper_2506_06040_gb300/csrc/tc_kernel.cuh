@@ -46,10 +46,13 @@ __device__ __forceinline__ int64_t frame_pixel(const TcArgs& p, const WorkChunk&
     const int ft = __ldg(p.ulist + c.first + T);
     const int ty = ft / p.tiles_x, tx = ft - ty * p.tiles_x;
     const int r = gt / p.tile_w;
-    const int64_t px = (int64_t)(ty * p.tile_h + r) * p.frame_w + tx * p.tile_w + (gt - r * p.tile_w);
+    int64_t px = (int64_t)(ty * p.tile_h + r) * p.frame_w + tx * p.tile_w + (gt - r * p.tile_w);
+    NBTC_CHECK_INDEX(px, p.frame_pixels, p.d.status);
     return __ldg(p.fmat + px) == c.mat ? px : -1;
   }
-  return __ldg(p.plist + (c.first + T) * 128 + gt);
+  int64_t px = __ldg(p.plist + (c.first + T) * 128 + gt);
+  if (px >= 0) NBTC_CHECK_INDEX(px, p.frame_pixels, p.d.status);
+  return px;
 }
 
 // Shared-memory plan.  Per slot: A0 (128 x K operand of layer 1) and Ah

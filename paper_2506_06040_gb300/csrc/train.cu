@@ -58,6 +58,8 @@ struct TrainDev {
   float* part;      // [gridDim.x][kPart]
   const float* xt;  // pre-gathered samples [batch][rs] (features, then target channels), or null
   int rs;           // floats per pre-gathered sample
+  int* status;      // checked build: status word the bounds checks record to
+  int plant;        // checked build, tests only: offset added to every tap index (0 otherwise)
 };
 
 // Neumaier: (s, e) += x, exact sum ~ s + e
@@ -91,6 +93,27 @@ __device__ __forceinline__ Taps clamp_taps(float u, float v, int w, int h, float
   t.w01 = (1.f - fx) * fy;
   t.w11 = fx * fy;
   return t;
+}
+
+// Checked build: the tap indices of a texture of n texels against its extent
+// (plus the test-only offset); compiled away otherwise.
+__device__ __forceinline__ void check_taps(Taps& T, int64_t n, const TrainDev& a) {
+#ifdef NBTC_CHECKED
+  int64_t i00 = (int64_t)T.i00 + a.plant, i10 = (int64_t)T.i10 + a.plant;
+  int64_t i01 = (int64_t)T.i01 + a.plant, i11 = (int64_t)T.i11 + a.plant;
+  NBTC_CHECK_INDEX(i00, n, a.status);
+  NBTC_CHECK_INDEX(i10, n, a.status);
+  NBTC_CHECK_INDEX(i01, n, a.status);
+  NBTC_CHECK_INDEX(i11, n, a.status);
+  T.i00 = (int)i00;
+  T.i10 = (int)i10;
+  T.i01 = (int)i01;
+  T.i11 = (int)i11;
+#else
+  (void)T;
+  (void)n;
+  (void)a;
+#endif
 }
 
 // Shared memory of k_train: weights in both orientations (forward products
@@ -190,7 +213,8 @@ template <bool LV>
 __device__ __forceinline__ void sample_features(const TrainDev& a, float u, float v, float (&f)[kIn]) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const Taps T = clamp_taps(u, v, a.lw[k], a.lh[k], a.shift[k]);
+    Taps T = clamp_taps(u, v, a.lw[k], a.lh[k], a.shift[k]);
+    check_taps(T, (int64_t)a.lw[k] * a.lh[k], a);
     const float* L = a.lat[k];
     if constexpr (LV) {
       const float4* L4 = reinterpret_cast<const float4*>(L);
@@ -211,7 +235,8 @@ __device__ __forceinline__ void sample_features(const TrainDev& a, float u, floa
 // out[c * stride]; TV: 16-byte reads of a texel stride that is a multiple of 4.
 template <bool TV>
 __device__ __forceinline__ void sample_target(const TrainDev& a, float u, float v, float* out, int stride) {
-  const Taps T = clamp_taps(u, v, a.tw, a.th, 0.f);
+  Taps T = clamp_taps(u, v, a.tw, a.th, 0.f);
+  check_taps(T, (int64_t)a.tw * a.th, a);
   const size_t ts = (size_t)a.ts;
   const int C = a.C;
   if constexpr (TV) {
@@ -543,7 +568,8 @@ __global__ void __launch_bounds__(kTT, 1) k_train(TrainDev a) {
       if (valid) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
+          Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
+          check_taps(T, (int64_t)a.lw[k] * a.lh[k], a);
           float* G = a.lgrad[k];
           if constexpr (LV) {
             float4* G4 = reinterpret_cast<float4*>(G);
@@ -728,7 +754,8 @@ __global__ void __launch_bounds__(256) k_scatter_probe(TrainDev a) {
   const float g = 1e-3f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
+    Taps T = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
+    check_taps(T, (int64_t)a.lw[k] * a.lh[k], a);
     float* G = a.lgrad[k];
     if constexpr (LV) {
       float4* G4 = reinterpret_cast<float4*>(G);
@@ -817,6 +844,8 @@ size_t train_workspace(nbtc_context* ctx, const nbtc_train_args* A) {
 
 static TrainDev make_dev(const nbtc_train_args* A, void* workspace) {
   TrainDev d;
+  d.status = nullptr;
+  d.plant = 0;
   for (int k = 0; k < 4; ++k) {
     d.lat[k] = A->latents[k];
     d.lgrad[k] = A->latent_grads[k];
@@ -916,6 +945,8 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
   if (st) return st;
   const int grid = train_grid(ctx, A->batch);
   TrainDev d = make_dev(A, workspace);
+  d.status = ctx->status_dev;
+  d.plant = ctx->check_plant;
   if (mode == kModeFwd) {
     if (A->batch == 0) return NBTC_OK;
     if (!y) return fail(NBTC_ERR_INVALID_ARG, "y is NULL");
@@ -1037,7 +1068,9 @@ extern "C" nbtc_status nbtc_probe_scatter(nbtc_context* ctx, const nbtc_train_ar
   if ((st = enter(ctx))) return st;
   if ((st = check_train(args, false, false, false))) return st;
   if (args->batch == 0) return NBTC_OK;
-  const TrainDev d = make_dev(args, nullptr);
+  TrainDev d = make_dev(args, nullptr);
+  d.status = ctx->status_dev;
+  d.plant = ctx->check_plant;
   const unsigned grid = (unsigned)((args->batch + 255) / 256);
   if (latent_stride(args) == 4)
     k_scatter_probe<true><<<grid, 256, 0, (cudaStream_t)stream>>>(d);
