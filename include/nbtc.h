@@ -60,14 +60,19 @@ typedef enum {
  * accumulator: every multiply still reads the narrow format, at three times
  * the tensor work, and the result keeps most of the precision the single
  * rounding loses (max abs error vs FP64 on a He-initialised 12-64-64-64-9
- * decode: FP16 3.2e-3 -> 9.8e-4, the FP16 output rounding; E4M3 0.37 -> 1.2e-2). */
+ * decode: FP16 3.2e-3 -> 9.8e-4, the FP16 output rounding; E4M3 0.37 -> 1.2e-2;
+ * before the output rounding the FP16 split is within ~1e-6, which NBTC_FP32_TC
+ * keeps by writing FP32). */
 typedef enum {
   NBTC_FP32 = 0,            /* FP32 SIMT arithmetic (FFMA), FP32 output              */
   NBTC_FP16 = 1,            /* FP16 operands on tcgen05, FP32 accumulate, FP16 output */
   NBTC_FP8_E4M3 = 2,        /* E4M3 operands on tcgen05 with per-layer power-of-two
                                scales, FP32 accumulate, FP16 output                   */
   NBTC_FP16_SPLIT = 3,      /* split FP16 operands, otherwise as NBTC_FP16            */
-  NBTC_FP8_E4M3_SPLIT = 4   /* split E4M3 operands, otherwise as NBTC_FP8_E4M3        */
+  NBTC_FP8_E4M3_SPLIT = 4,  /* split E4M3 operands, otherwise as NBTC_FP8_E4M3        */
+  NBTC_FP32_TC = 5          /* split FP16 operands on tcgen05 as NBTC_FP16_SPLIT, the
+                               FP32 accumulator written as FP32 output (no FP16
+                               rounding): FP32-form accuracy on tensor cores       */
 } nbtc_precision;
 
 typedef enum { NBTC_CLAMP = 0, NBTC_WRAP = 1 } nbtc_address;
@@ -204,7 +209,8 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
  *  - precision NBTC_FP32: `packed_dev` NULL, `out_dev` n x N FP32.
  *    NBTC_FP16 / NBTC_FP8_E4M3 / NBTC_FP16_SPLIT / NBTC_FP8_E4M3_SPLIT:
  *    `packed_dev` from nbtc_pack_mlp() with the same precision, `out_dev`
- *    n x N FP16.  out_dev 16-byte aligned.
+ *    n x N FP16.  NBTC_FP32_TC: `packed_dev` from nbtc_pack_mlp() with
+ *    NBTC_FP32_TC, `out_dev` n x N FP32.  out_dev 16-byte aligned.
  *  - Inputs (level blocks, MLP weights and biases, uv_dev) are device memory or
  *    pinned host memory (read over the host link); packed_dev is device memory
  *    (it is bulk-copied into shared memory); anything else is
@@ -213,7 +219,7 @@ nbtc_status nbtc_fp8_calibrate(nbtc_context* ctx, const nbtc_latents* lat, const
  *    (cudaHostAlloc / cudaHostRegister): the kernel then stores the texels
  *    straight into host memory over the host link, with no staging buffer or
  *    copy; completion is the stream's.  Pinned host output with a tensor-core
- *    precision is NBTC_ERR_UNSUPPORTED (their kernels store with bulk
+ *    precision (NBTC_FP32_TC included) is NBTC_ERR_UNSUPPORTED (their kernels store with bulk
  *    copies, kept to device memory); any other pointer (pageable host memory)
  *    is NBTC_ERR_INVALID_ARG.
  * Shapes with a kernel: 4 latent levels, hidden width 16, 32 or 64 (all

@@ -16,7 +16,7 @@ LIB_CHECKED_PATH = os.path.join(HERE, "libnbtc_checked.so")
 
 MAX_LEVELS, MAX_LAYERS, MAX_MIPS = 8, 4, 16
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_BOUNDS = range(6)
-FP32, FP16, FP8_E4M3, FP16_SPLIT, FP8_E4M3_SPLIT = 0, 1, 2, 3, 4
+FP32, FP16, FP8_E4M3, FP16_SPLIT, FP8_E4M3_SPLIT, FP32_TC = 0, 1, 2, 3, 4, 5
 CLAMP, WRAP = 0, 1
 LOSS_MSE, LOSS_L1 = 0, 1
 

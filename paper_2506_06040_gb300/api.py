@@ -153,7 +153,7 @@ def decode(ctx: Context, mat: Material, precision: int = _abi.FP32, packed=None,
     if rows is not None:
         gw, gh = grid
         r0, nr = rows
-        dt = torch.float32 if precision == _abi.FP32 else torch.float16
+        dt = torch.float32 if precision in (_abi.FP32, _abi.FP32_TC) else torch.float16
         if out is None:
             out = torch.empty((nr * gw, mat.n_out), dtype=dt, device=mat.device)
         lat, m = mat.latents_struct(), mat.mlp_struct()
@@ -166,7 +166,7 @@ def decode(ctx: Context, mat: Material, precision: int = _abi.FP32, packed=None,
     else:
         gw, gh = grid
         n = gw * gh
-    dt = torch.float32 if precision == _abi.FP32 else torch.float16
+    dt = torch.float32 if precision in (_abi.FP32, _abi.FP32_TC) else torch.float16
     if out is None:
         out = torch.empty((n, mat.n_out), dtype=dt, device=mat.device)
     lat, m = mat.latents_struct(), mat.mlp_struct()
@@ -191,7 +191,7 @@ def decode_to_host(ctx: Context, mat: Material, host_out: torch.Tensor, grid, pr
         return decode(ctx, mat, precision, packed, grid=grid, out=host_out, stream=stream)
     copy_stream = copy_stream or torch.cuda.Stream()
     per = -(-gh // bands)
-    dt = torch.float32 if precision == _abi.FP32 else torch.float16
+    dt = torch.float32 if precision in (_abi.FP32, _abi.FP32_TC) else torch.float16
     bufs = [torch.empty((per * gw, mat.n_out), dtype=dt, device=mat.device) for _ in range(2)]
     done = [torch.cuda.Event(), torch.cuda.Event()]     # band decoded
     freed = [torch.cuda.Event(), torch.cuda.Event()]    # band buffer copied out

@@ -311,10 +311,16 @@ static nbtc_status resolve_out(int32_t precision, DecodeArgs& a) {
     cudaGetLastError();
     return fail(NBTC_ERR_INVALID_ARG, "out is not a pointer CUDA knows");
   }
-  if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) return NBTC_OK;
+  if (pa.type == cudaMemoryTypeManaged) return NBTC_OK;
+  if (pa.type == cudaMemoryTypeDevice) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && pa.device == dev) return NBTC_OK;
+    return fail(NBTC_ERR_INVALID_ARG, "out is device memory of another GPU");
+  }
   if (pa.type == cudaMemoryTypeHost && pa.devicePointer) {
     if (precision != NBTC_FP32)
-      return fail(NBTC_ERR_UNSUPPORTED, "pinned host output is for FP32 decodes; FP16 / FP8 decode into device memory");
+      return fail(NBTC_ERR_UNSUPPORTED,
+                  "pinned host output is for the FP32 SIMT decode; tensor-core forms decode into device memory");
     a.out = pa.devicePointer;
     if (!aligned(a.out, 16)) return fail(NBTC_ERR_INVALID_ARG, "out not 16-byte aligned");
     return NBTC_OK;
@@ -339,6 +345,7 @@ nbtc_status nbtc_decode(nbtc_context* ctx, const nbtc_latents* lat, const nbtc_m
     case NBTC_FP8_E4M3:
     case NBTC_FP16_SPLIT:
     case NBTC_FP8_E4M3_SPLIT:
+    case NBTC_FP32_TC:
       if ((st = need_device(packed_dev, "packed MLP"))) return st;
       return launch_decode_tc(ctx, a, mlp, precision, packed_dev, (cudaStream_t)stream);
     default:
@@ -367,6 +374,7 @@ nbtc_status nbtc_decode_rows(nbtc_context* ctx, const nbtc_latents* lat, const n
     case NBTC_FP8_E4M3:
     case NBTC_FP16_SPLIT:
     case NBTC_FP8_E4M3_SPLIT:
+    case NBTC_FP32_TC:
       if ((st = need_device(packed_dev, "packed MLP"))) return st;
       return launch_decode_tc(ctx, a, mlp, precision, packed_dev, (cudaStream_t)stream);
     default:
@@ -382,7 +390,7 @@ nbtc_status nbtc_packed_mlp_bytes(const nbtc_mlp* mlp, int32_t precision, size_t
     *bytes = 0;
     return NBTC_OK;
   }
-  if (precision < NBTC_FP16 || precision > NBTC_FP8_E4M3_SPLIT) return fail(NBTC_ERR_INVALID_ARG, "unknown precision");
+  if (precision < NBTC_FP16 || precision > NBTC_FP32_TC) return fail(NBTC_ERR_INVALID_ARG, "unknown precision");
   return tc_packed_bytes(mlp, precision, bytes);
 }
 
@@ -393,8 +401,8 @@ nbtc_status nbtc_pack_mlp(nbtc_context* ctx, const nbtc_mlp* mlp, int32_t precis
   nbtc_status st = enter(ctx);
   if (st) return st;
   if ((st = check_mlp(mlp))) return st;
-  if (precision < NBTC_FP16 || precision > NBTC_FP8_E4M3_SPLIT)
-    return fail(NBTC_ERR_INVALID_ARG, "pack_mlp takes a tensor-core precision (FP16, E4M3 or their split forms)");
+  if (precision < NBTC_FP16 || precision > NBTC_FP32_TC)
+    return fail(NBTC_ERR_INVALID_ARG, "pack_mlp takes a tensor-core precision");
   // the packed image is later bulk-copied into shared memory: device memory only
   if ((st = need_inputs(nullptr, mlp)) || (st = need_device(packed_dev, "packed MLP"))) return st;
   if (act_absmax_dev && (st = need_readable(act_absmax_dev, "act_absmax"))) return st;

@@ -87,7 +87,7 @@ __global__ void k_pack_mlp(const float* __restrict__ W, const float* __restrict_
           *reinterpret_cast<__half*>(out + L.off_w1() + off_ilv(n, 2 * k, R1)) = __float2half_rn(w);
         } else if (form == kF8) {
           out[L.off_w1() + off_ilv(n, k, R1)] = (unsigned char)(cvt_e4m3x2(w, 0.f) & 0xFF);
-        } else if (form == kF16Split) {
+        } else if (L.f16split()) {
           const WParts q = weight_parts(w);
           *reinterpret_cast<uint16_t*>(out + L.off_w1() + off_ilv(n, 2 * k, R1)) = q.h16;
           *reinterpret_cast<uint16_t*>(out + L.off_w1() + off_ilv(n, 2 * (16 + k), R1)) = q.h16;
@@ -184,6 +184,7 @@ static int tc_form(int precision) {
     case NBTC_FP16: return kF16;
     case NBTC_FP8_E4M3: return kF8;
     case NBTC_FP16_SPLIT: return kF16Split;
+    case NBTC_FP32_TC: return kF32Split;
     case NBTC_FP8_E4M3_SPLIT: return kF8Split;
   }
   return -1;
@@ -230,6 +231,9 @@ NBTC_TC_UNIT(launch_tc_h3_f16s)
 NBTC_TC_UNIT(launch_tc_h1_f8s)
 NBTC_TC_UNIT(launch_tc_h2_f8s)
 NBTC_TC_UNIT(launch_tc_h3_f8s)
+NBTC_TC_UNIT(launch_tc_h1_f32s)
+NBTC_TC_UNIT(launch_tc_h2_f32s)
+NBTC_TC_UNIT(launch_tc_h3_f32s)
 NBTC_TC_UNIT(launch_tc_h1_f16_batch)
 NBTC_TC_UNIT(launch_tc_h2_f16_batch)
 NBTC_TC_UNIT(launch_tc_h3_f16_batch)
@@ -245,19 +249,20 @@ nbtc_status launch_tc_args(nbtc_context* ctx, const TcArgs& p, int nhid, int for
     static const Fn batch[3] = {launch_tc_h1_f16_batch, launch_tc_h2_f16_batch, launch_tc_h3_f16_batch};
     return batch[nhid - 1](p, W, slots, grid, s);
   }
-  static const Fn single[4][3] = {{launch_tc_h1_f16, launch_tc_h2_f16, launch_tc_h3_f16},
+  static const Fn single[5][3] = {{launch_tc_h1_f16, launch_tc_h2_f16, launch_tc_h3_f16},
                                   {launch_tc_h1_f8, launch_tc_h2_f8, launch_tc_h3_f8},
                                   {launch_tc_h1_f16s, launch_tc_h2_f16s, launch_tc_h3_f16s},
-                                  {launch_tc_h1_f8s, launch_tc_h2_f8s, launch_tc_h3_f8s}};
-  if (form < 0 || form > 3) return fail(NBTC_ERR_INVALID_ARG, "not a tensor-core precision");
+                                  {launch_tc_h1_f8s, launch_tc_h2_f8s, launch_tc_h3_f8s},
+                                  {launch_tc_h1_f32s, launch_tc_h2_f32s, launch_tc_h3_f32s}};
+  if (form < 0 || form > 4) return fail(NBTC_ERR_INVALID_ARG, "not a tensor-core precision");
   return single[form][nhid - 1](p, W, slots, grid, s);
 }
 
 // Warpgroups and tile slots per CTA of a form: two slots of 3 or 4 warpgroups
-// (context setting), except the FP16 split form, whose two A tiles per slot
+// (context setting), except the split-FP16 forms, whose two A tiles per slot
 // leave shared memory for 4 x 1 (default) or 2 x 2.
 static void tc_shape_of(const nbtc_context* ctx, int form, int& W, int& slots) {
-  if (form == kF16Split) {
+  if (form == kF16Split || form == kF32Split) {
     W = ctx->tc_groups == 2 ? 2 : 4;
     slots = W == 2 ? 2 : 1;
   } else {

@@ -16,7 +16,12 @@ constexpr int kMaxOut = 16;
 // Operand forms of the tensor-core decode.  The split forms carry every weight
 // and activation as a pair hi + lo of the narrow format and run three products
 // per layer into one FP32 accumulator: hi(A) hi(W) + lo(A) hi(W) + hi(A) lo(W).
-enum TcForm { kF16 = 0, kF8 = 1, kF16Split = 2, kF8Split = 3 };
+// kF32Split is kF16Split with the output layer's FP32 accumulator written as
+// FP32 (no output rounding): the FP32-accurate form.
+enum TcForm { kF16 = 0, kF8 = 1, kF16Split = 2, kF8Split = 3, kF32Split = 4 };
+
+// Bytes of per-warp output staging: 32 texels x up to 16 channels of FP16, or FP32.
+__host__ __device__ constexpr int stage_bytes(int form) { return form == kF32Split ? 2048 : 1024; }
 
 // Byte layout of a packed MLP (identical in global memory and shared memory).
 // FP16 forms: every layer's bias enters the MMA as FP16 operand(s) -- layer 1
@@ -36,11 +41,12 @@ struct TcLayout {
   int nhid;   // hidden layers (1..3)
   int form;   // TcForm
   __host__ __device__ bool fp8() const { return form == kF8 || form == kF8Split; }
-  __host__ __device__ bool split() const { return form == kF16Split || form == kF8Split; }
+  __host__ __device__ bool f16split() const { return form == kF16Split || form == kF32Split; }
+  __host__ __device__ bool split() const { return f16split() || form == kF8Split; }
   __host__ __device__ int esz() const { return fp8() ? 1 : 2; }
   __host__ __device__ int parts() const { return split() ? 2 : 1; }
-  __host__ __device__ int w1_row() const { return form == kF16Split ? 96 : form == kF8Split ? 64 : 32; }
-  __host__ __device__ int a0_row() const { return form == kF16Split ? 64 : 32; }
+  __host__ __device__ int w1_row() const { return f16split() ? 96 : form == kF8Split ? 64 : 32; }
+  __host__ __device__ int a0_row() const { return f16split() ? 64 : 32; }
   __host__ __device__ int wh_part() const { return kHid * kHid * esz(); }                // 64 x 64
   __host__ __device__ int wh_bytes() const { return parts() * wh_part(); }
   __host__ __device__ int bth_bytes() const { return fp8() ? 0 : kHid * 16 * 2; }       // 64 x 16 bias tile
@@ -125,7 +131,6 @@ struct TcWork {
   int reload;
 };
 
-constexpr int kStageBytes = 1024;  // per-warp output staging (32 texels x <= 16 halves)
 
 
 struct TcArgs;

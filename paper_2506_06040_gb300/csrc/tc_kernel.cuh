@@ -81,7 +81,7 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W, int NSL) {
   s.image = (L.bytes() + 1023) & ~1023;
   s.ones = s.image;
   s.slots = s.ones + 4096;
-  if (L.form == kF16Split) {
+  if (L.f16split()) {
     s.a0 = 0;
     s.ah = 0;
     s.ah_lo = 16384;
@@ -95,7 +95,7 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W, int NSL) {
     s.slot = 4096 + 16384;
   }
   s.stage = s.slots + NS * s.slot;
-  s.bars = s.stage + W * 4 * kStageBytes;
+  s.bars = s.stage + W * 4 * stage_bytes(L.form);
   s.tslot = s.bars + (2 * NS + 1) * 8;
   s.work = (s.tslot + 16 + 15) & ~15;
   s.total = s.work + (int)((sizeof(TcWork) + 15) & ~(size_t)15) + 1024 /* alignment slack */;
@@ -124,7 +124,9 @@ template <int NHID, int FORM, int W, int MODE, int NSL>
 __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   constexpr TcLayout L{NHID, FORM};
   constexpr bool FP8 = FORM == kF8 || FORM == kF8Split;
-  constexpr bool SPLIT = FORM == kF16Split || FORM == kF8Split;
+  constexpr bool F16S = FORM == kF16Split || FORM == kF32Split;  // split FP16 operands
+  constexpr bool SPLIT = F16S || FORM == kF8Split;
+  constexpr bool OUT32 = FORM == kF32Split;                      // FP32 output
   constexpr int kSlots = NSL;
   constexpr int NS = W * kSlots;
   constexpr uint32_t kTmemCols = NS * kHid <= 256 ? 256 : 512;
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
                 // K chunks of 32 bytes (16 FP16 / 32 E4M3), 256 bytes apart in
                 // the no-swizzle layout
                 const uint32_t la = lo(slot + S.a0, 128);
-                if constexpr (FORM == kF16Split) {
+                if constexpr (F16S) {
                   mma_f16(d, dsc(hi_a0, la), dsc(hi_w1, lo_w1), ID_HID, 0);                // hi x . hi W + hi b
                   mma_f16(d, dsc(hi_a0, la + 16), dsc(hi_w1, lo_w1 + 16), ID_HID, 1);      // lo x . hi W + lo b
                   mma_f16(d, dsc(hi_a0, la), dsc(hi_w1, lo_w1 + 32), ID_HID, 1);           // hi x . lo W
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       const int gt = tid % kTile;
       const int bar_id = 1 + wg;
       const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
-      const uint32_t stage_s = sbase + S.stage + warp * kStageBytes;
+      const uint32_t stage_s = sbase + S.stage + warp * stage_bytes(FORM);
       const float* bias = reinterpret_cast<const float*>(smem + L.off_bias());
       const float* alpha = reinterpret_cast<const float*>(smem + L.off_alpha());
       const DecodeArgs& D = MODE == kModeSingle ? p.d : work.m.d;
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
                  cvt_f16x2(f[6], f[7]));
           sts128(a0 + off_interleave(gt, 16), cvt_f16x2(f[8], f[9]), cvt_f16x2(f[10], f[11]),
                  0x3C00u /* k = 12: 1.0 for the bias */, 0u);
-        } else if constexpr (FORM == kF16Split) {
+        } else if constexpr (F16S) {
           uint32_t h[6], r[6];
 #pragma unroll
           for (int i = 0; i < 6; ++i) split_f16x2(f[2 * i], f[2 * i + 1], h[i], r[i]);
@@ -409,10 +411,10 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
         const uint32_t ah = sbase + S.slots + q * S.slot + S.ah;
         const float alp = alpha[l];
         const float* b = bias + l * kHid;
+        // after a timed-out wait the loads still run (they cannot fault) and the
+        // results are discarded with the status
         // the accumulator row comes out of TMEM in two 32-column parts, one wait
-        // each (one 64-column load would spill registers); after a timed-out
-        // wait the loads still run (they cannot fault) and the results are
-        // discarded with the status
+        // each (measured faster than one 64-column load and one wait)
         constexpr int kParts = 2;
         constexpr int kPc = kHid / kParts;
 #pragma unroll
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
                      cvt_relu_f16x2(__uint_as_float(r[j + 4]), __uint_as_float(r[j + 5])),
                      cvt_relu_f16x2(__uint_as_float(r[j + 6]), __uint_as_float(r[j + 7])));
             }
-          } else if constexpr (FORM == kF16Split) {
+          } else if constexpr (F16S) {
 #pragma unroll
             for (int c = 0; c < kPc / 8; ++c) {
               const int j = 8 * c;
@@ -498,7 +500,31 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
 #pragma unroll
           for (int k = 0; k < kMaxOut; ++k) hv[k] = __half_as_ushort(__float2half_rn(__uint_as_float(r[k])));
         }
-        if (MODE == kModeSingle || grid_chunk) {
+        if constexpr (OUT32) {
+          // FP32 output (single-material grids and uv lists): the accumulator as is
+          const int64_t t0 = tile_first_texel(D, hdiv, footprint, work.c.first + T);
+          const int64_t tex = t0 + gt;
+          if (t0 + kTile <= D.n) {
+            // the warp's 32 texels x nout floats are contiguous: one bulk copy of
+            // 128 nout bytes at a 128-byte multiple of the 16-byte aligned output
+            if (lane == 0) bulk_wait_read0();
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < kMaxOut; ++k)
+              if (k < nout) sts32(stage_s + 4u * (uint32_t)(lane * nout + k), r[k]);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              bulk_s2g(reinterpret_cast<float*>(D.out) + (t0 + 32 * wq) * nout, stage_s, 128u * (uint32_t)nout);
+              bulk_commit();
+            }
+          } else if (tex < D.n) {
+            float* o = reinterpret_cast<float*>(D.out) + tex * nout;
+#pragma unroll
+            for (int k = 0; k < kMaxOut; ++k)
+              if (k < nout) o[k] = __uint_as_float(r[k]);
+          }
+        } else if (MODE == kModeSingle || grid_chunk) {
           const int64_t t0 = tile_first_texel(D, hdiv, footprint, work.c.first + T);
           const int64_t tex = t0 + gt;
           if (t0 + kTile <= D.n) {

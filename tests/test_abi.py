@@ -47,7 +47,8 @@ def test_struct_layouts_match_c():
              ("nbtc_frame", _abi.Frame), ("nbtc_batch_info", _abi.BatchInfo)]
     lines, want = [], []
     for cname, val in [("NBTC_FP32", _abi.FP32), ("NBTC_FP16", _abi.FP16), ("NBTC_FP8_E4M3", _abi.FP8_E4M3),
-                       ("NBTC_FP16_SPLIT", _abi.FP16_SPLIT), ("NBTC_FP8_E4M3_SPLIT", _abi.FP8_E4M3_SPLIT)]:
+                       ("NBTC_FP16_SPLIT", _abi.FP16_SPLIT), ("NBTC_FP8_E4M3_SPLIT", _abi.FP8_E4M3_SPLIT),
+                       ("NBTC_FP32_TC", _abi.FP32_TC)]:
         lines.append(f'  printf("%d\\n", (int){cname});')
         want.append(val)
     for cname, cls in pairs:
@@ -83,14 +84,15 @@ def test_host_only_checks(lib):
     m.weights, m.biases = 16, 16
     assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), _abi.FP32, ctypes.byref(n)) == _abi.OK and n.value == 0
     sizes = {}
-    for prec in (_abi.FP16, _abi.FP8_E4M3, _abi.FP16_SPLIT, _abi.FP8_E4M3_SPLIT):
+    for prec in (_abi.FP16, _abi.FP8_E4M3, _abi.FP16_SPLIT, _abi.FP8_E4M3_SPLIT, _abi.FP32_TC):
         assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), prec, ctypes.byref(n)) == _abi.OK
         sizes[prec] = n.value
         assert n.value % 16 == 0
     # the split forms store hi and lo of every weight tile
     assert sizes[_abi.FP16_SPLIT] > sizes[_abi.FP16] > sizes[_abi.FP8_E4M3]
     assert sizes[_abi.FP8_E4M3_SPLIT] > sizes[_abi.FP8_E4M3]
-    assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), 5, ctypes.byref(n)) == _abi.ERR_INVALID_ARG
+    assert sizes[_abi.FP32_TC] == sizes[_abi.FP16_SPLIT]   # the same operands, FP32 output
+    assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), 6, ctypes.byref(n)) == _abi.ERR_INVALID_ARG
     m.num_layers = 7
     assert lib.nbtc_packed_mlp_bytes(ctypes.byref(m), _abi.FP32, ctypes.byref(n)) == _abi.ERR_INVALID_ARG
     assert b"num_layers" in lib.nbtc_last_error()
