@@ -306,6 +306,104 @@ __device__ __forceinline__ void strip_features(const DecodeArgs& a, int j, int i
   }
 }
 
+// ---- row-footprint feature stage of one warp, with the latent columns shared
+// between its lanes by shuffles.  The warp's 32 consecutive texels of one
+// output row read at most ceil(31 W_k / W_out) + 2 columns of level k: 23 jobs
+// over the four levels of the 1/4..1/32 pyramid, 32 for 1/4, 1/4, 1/8, 1/8.
+// Lane L owns column job L (the strip cache above, per warp: it keeps its two
+// decoded texels across rows and re-decodes only when the vertical tap pair
+// moves), blends them vertically once per row, and each texel reads its two
+// horizontal neighbours from the lanes that hold them -- no shared memory and
+// no barrier across warps.  A footprint of more than 32 jobs (level-to-output
+// ratios above ~1/4) samples each texel on its own.
+__device__ __forceinline__ void direct_features(const DecodeArgs& a, int64_t t, float (&feat)[12]);
+
+__device__ __forceinline__ void warp_strip_features(const DecodeArgs& a, int j, int i0w, int lane, StripCache& C,
+                                                    float (&feat)[12]) {
+  const float s = 1.0f / 255.0f;
+  if (i0w != C.i0) {  // new strip: the warp's column plan, own job, own texel's source lanes
+    C.i0 = i0w;
+    C.key = INT_MIN + 1;
+    const float u0 = grid_coord((float)i0w, a.cw);
+    const float u1 = grid_coord((float)(i0w + 31), a.cw);
+    const float u = grid_coord((float)(i0w + lane), a.cw);
+    int total = 0, job = -1, jx = 0;
+    uint32_t src4 = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const LevelView& L = a.lv[k];
+      const int b0 = (int)floorf(texel_coord(u0, L.w, L.shift));
+      const int b1 = (int)floorf(texel_coord(u1, L.w, L.shift));
+      const int span = b1 - b0 + 2;
+      if (lane >= total && lane < total + span) {
+        job = k | (lane - total) << 2;
+        jx = wrap_or_clamp(b0 + lane - total, L.w, a.wrap);
+      }
+      const float tx = texel_coord(u, L.w, L.shift);
+      const float ftx = floorf(tx);
+      C.fx[k] = tx - ftx;
+      // floor is monotone in u, so the left tap's job lies in [0, span - 2]; the clamp only guards the lanes
+      src4 |= (uint32_t)min(total + min(max((int)ftx - b0, 0), span - 2), 30) << (8 * k);
+      total += span;
+    }
+    C.total = total;
+    C.job = job;
+    C.jx = jx;
+    C.rel4 = src4;
+  }
+  if (C.total > 32) {  // warp-uniform: a footprint wider than the warp's lanes
+    direct_features(a, (int64_t)j * a.grid_w + i0w + lane, feat);
+    return;
+  }
+  float cv0 = 0.f, cv1 = 0.f, cv2 = 0.f;
+  if (C.job >= 0) {
+    const int k = C.job & 3;
+    const LevelView& L = a.lv[k];
+    const float ty = texel_coord(grid_coord((float)(j + a.row0), a.ch), L.h, L.shift);
+    const float fty = floorf(ty);
+    const float fy = ty - fty;
+    const int key = (int)fty;
+    if (key != C.key) {
+      uint32_t t0;
+      if (key == C.key + 1) {
+        t0 = C.t1;
+      } else {
+        const int y0 = wrap_or_clamp(key, L.h, a.wrap);
+        t0 = bc1_texel(__ldg(L.blocks + block_index(L, C.jx >> 2, y0 >> 2)), C.jx & 3, y0 & 3);
+      }
+      const int y1 = wrap_or_clamp(key + 1, L.h, a.wrap);
+      const uint32_t t1 = bc1_texel(__ldg(L.blocks + block_index(L, C.jx >> 2, y1 >> 2)), C.jx & 3, y1 & 3);
+      C.key = key;
+      C.t1 = t1;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v0 = (float)((t0 >> (8 * c)) & 255u), v1 = (float)((t1 >> (8 * c)) & 255u);
+        C.c0[c] = s * v0;
+        C.dc[c] = s * (v1 - v0);
+      }
+    }
+    cv0 = fmaf(fy, C.dc[0], C.c0[0]);
+    cv1 = fmaf(fy, C.dc[1], C.c0[1]);
+    cv2 = fmaf(fy, C.dc[2], C.c0[2]);
+    const float tyn = texel_coord(grid_coord((float)(j + a.row0 + 1), a.ch), L.h, L.shift);
+    const int keyn = (int)floorf(tyn);
+    if (keyn != key && j + 1 < a.grid_h) {
+      const int y1 = wrap_or_clamp(keyn + 1, L.h, a.wrap);
+      sm100::prefetch_l1(L.blocks + block_index(L, C.jx >> 2, y1 >> 2));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int src = (C.rel4 >> (8 * k)) & 255;
+    const float a0 = __shfl_sync(0xffffffffu, cv0, src), b0 = __shfl_sync(0xffffffffu, cv0, src + 1);
+    const float a1 = __shfl_sync(0xffffffffu, cv1, src), b1 = __shfl_sync(0xffffffffu, cv1, src + 1);
+    const float a2 = __shfl_sync(0xffffffffu, cv2, src), b2 = __shfl_sync(0xffffffffu, cv2, src + 1);
+    feat[3 * k + 0] = fmaf(C.fx[k], b0 - a0, a0);
+    feat[3 * k + 1] = fmaf(C.fx[k], b1 - a1, a1);
+    feat[3 * k + 2] = fmaf(C.fx[k], b2 - a2, a2);
+  }
+}
+
 // Per-material description used by the batched and frame decodes: the level
 // views of mip 0 (in `d`) plus every level's mip chain for trilinear sampling.
 struct MatDev {

@@ -138,8 +138,8 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   const int tid = threadIdx.x;
   const int warp = tid / 32, lane = tid % 32;
   const uint32_t dbar0 = sbase + S.bars, wbar = dbar0 + NS * 8;
-  // named barriers: 0 = __syncthreads, 1 + g = warpgroup g's feature stage,
-  // 1 + W + q = A-ready of slot q
+  // named barriers: 0 = __syncthreads, 1 + W + q = A-ready of slot q (1 .. W
+  // unused: the feature stage shares latent columns within a warp)
   static_assert(1 + W + NS <= 16, "named barrier ids");
   auto bar_a = [](int q) { return 1 + W + q; };
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S.tslot);
@@ -322,7 +322,6 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       // ---------------------------------------------------------- warpgroups
       const int wg = warp / 4, wq = warp & 3;
       const int gt = tid % kTile;
-      const int bar_id = 1 + wg;
       const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
       const uint32_t stage_s = sbase + S.stage + warp * stage_bytes(FORM);
       const float* bias = reinterpret_cast<const float*>(smem + L.off_bias());
@@ -342,11 +341,11 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
         float f[12];
         if (MODE == kModeSingle || grid_chunk) {
           if (footprint) {
-            // tile number = column block x H + row; Ah is free: the previous
-            // tile's last MMA (which read it) has completed
+            // tile number = column block x H + row; each warp decodes its own
+            // 32 texels' latent columns and shares them by shuffles
             const uint32_t t = (uint32_t)(work.c.first + T), H = (uint32_t)D.grid_h;
             const uint32_t cb = fastdiv(t, hdiv);
-            strip_features<kTile>(D, (int)(t - cb * H), (int)cb * kTile, gt, a0 - S.a0 + S.colbuf, bar_id, cache, f);
+            warp_strip_features(D, (int)(t - cb * H), (int)cb * kTile + 32 * wq, lane, cache, f);
           } else {
             const int64_t tex = (work.c.first + T) * kTile + gt;
             direct_features(D, tex < D.n ? tex : D.n - 1, f);
