@@ -160,6 +160,7 @@ nbtc_status nbtc_create(int device, nbtc_context** out) {
   ctx->sm_count = prop.multiProcessorCount;
   if (const char* e = getenv("NBTC_TC_GROUPS")) ctx->tc_groups = atoi(e) == 3 ? 3 : atoi(e) == 2 ? 2 : 4;
   if (const char* e = getenv("NBTC_FP32_GROUPS")) ctx->fp32_groups = atoi(e) == 1 ? 1 : 2;
+  if (const char* e = getenv("NBTC_TRAIN_SIMT")) ctx->train_tc = atoi(e) == 1 ? 0 : 1;
   if ((st = cuda_check(cudaMalloc(&ctx->status_dev, sizeof(int)), "cudaMalloc(status)"))) {
     delete ctx;
     return st;

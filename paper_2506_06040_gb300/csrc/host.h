@@ -15,6 +15,7 @@ struct nbtc_context {
   int tc_groups = 4;               // warpgroups per CTA of the tensor-core decode (3 or 4)
   int fp32_groups = 2;             // independent thread groups per CTA of the FP32 wide decode (1 or 2)
   int check_plant = 0;             // checked build, tests only: offset added to gather indices
+  int train_tc = 1;                // training steps with pre-gathered samples on tensor cores (0: SIMT)
 };
 
 #include <nvtx3/nvToolsExt.h>

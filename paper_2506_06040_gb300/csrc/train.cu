@@ -116,6 +116,12 @@ __device__ __forceinline__ void check_taps(Taps& T, int64_t n, const TrainDev& a
 #endif
 }
 
+}  // namespace nbtc
+
+#include "train_tc.cuh"
+
+namespace nbtc {
+
 // Shared memory of k_train: weights in both orientations (forward products
 // read W^T rows, backward products read W rows, both as broadcast 128-bit
 // loads), biases, and the tile's activations feature-major [row][sample]:
@@ -965,6 +971,14 @@ nbtc_status train_step_impl(nbtc_context* ctx, const nbtc_train_args* A, float* 
     if (!dy && A->batch > 0) return fail(NBTC_ERR_INVALID_ARG, "dy is NULL");
     d.dy = dy;
     if ((st = launch_train_kernel<kModeBwd>(A, d, grid, s))) return st;
+  } else if (d.xt && ctx->train_tc) {
+    // pre-gathered records: the tensor-core kernel (two 128-sample warpgroups per CTA)
+    auto kern = latent_stride(A) == 4 ? k_train_tc<true> : k_train_tc<false>;
+    if ((st = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, ttc::kSmem),
+                         "smem attr")))
+      return st;
+    kern<<<grid, ttc::kWG * 160, ttc::kSmem, s>>>(d);
+    if ((st = cuda_check(cudaGetLastError(), "launch k_train_tc"))) return st;
   } else {
     if ((st = launch_train_kernel<kModeTrain>(A, d, grid, s))) return st;
   }

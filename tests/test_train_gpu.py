@@ -258,34 +258,75 @@ def test_layouts_give_the_same_step(nb, ctx):
         assert (g3 - g4).abs().max().item() <= 1e-6 * g3.abs().max().item()
 
 
-def test_pre_gathered_and_fused_gather_agree(nb, ctx):
-    """With a workspace that has room for the batch, the step gathers every
-    sample's features and target into the workspace first (k_gather); with one
-    that only holds the partial sums it gathers inside the training kernel.
-    Same arithmetic: the same loss and MLP gradients bit for bit."""
+@pytest.fixture(scope="module")
+def simt_ctx(nb):
+    """A context whose steps run every sample on the FP32 SIMT training kernel
+    (NBTC_TRAIN_SIMT=1, read when the context is created)."""
+    import os
+    os.environ["NBTC_TRAIN_SIMT"] = "1"
+    try:
+        c = nb.Context(0)
+    finally:
+        del os.environ["NBTC_TRAIN_SIMT"]
+    yield c
+    c.close()
+
+
+def _raw_step(ctx, wl, uv, tgt, partials_only):
+    """One nbtc_train_step on a fresh model; partials_only: a workspace with room
+    for the per-CTA partial sums only (2 x 6033 floats per CTA, one CTA per
+    256-sample tile or SM), so the step gathers inside its main kernel."""
     import ctypes
-    from paper_2506_06040_gb300.train import ContinuousModel, padded
+    from paper_2506_06040_gb300.train import ContinuousModel
+    m = ContinuousModel.from_synth(wl)
+    a = m.args(uv, tgt)
+    m._workspace(ctx, a)
+    if partials_only:
+        grid = min(-(-int(uv.shape[0]) // 256), torch.cuda.get_device_properties(0).multi_processor_count)
+        a.workspace_bytes = grid * 2 * 6033 * 4
+    loss = torch.empty(1, device="cuda")
+    assert ctx.lib.nbtc_train_step(ctx.handle, ctypes.byref(a), ctypes.c_void_p(loss.data_ptr()),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    ctx.sync()
+    return loss.clone(), m.grad_w.clone(), m.grad_b.clone(), [g.clone() for g in m.latent_grads]
+
+
+def test_pre_gathered_and_fused_gather_agree(nb, simt_ctx):
+    """On the SIMT kernel, a workspace with room for the batch makes the step
+    gather every sample's features and target first (k_gather); one that only
+    holds the partial sums makes it gather inside the training kernel.  Same
+    arithmetic: the same loss and MLP gradients bit for bit."""
+    from paper_2506_06040_gb300.train import padded
     wl = _mid_workload(seed=79)
     uv = torch.from_numpy(wl.uv(0)).cuda()
     tgt = padded(torch.from_numpy(wl.target).cuda())
-    losses, grads = [], []
-    for small in (False, True):
-        m = ContinuousModel.from_synth(wl)
-        a = m.args(uv, tgt)
-        m._workspace(ctx, a)
-        if small:   # room for the per-CTA partial sums only (2 x 6033 floats per CTA, one CTA per tile or SM)
-            grid = min(-(-int(uv.shape[0]) // 256), torch.cuda.get_device_properties(0).multi_processor_count)
-            a.workspace_bytes = grid * 2 * 6033 * 4
-        loss = torch.empty(1, device="cuda")
-        assert ctx.lib.nbtc_train_step(ctx.handle, ctypes.byref(a), ctypes.c_void_p(loss.data_ptr()),
-                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
-        ctx.sync()
-        losses.append(loss.clone())
-        grads.append((m.grad_w.clone(), m.grad_b.clone(), [g.clone() for g in m.latent_grads]))
-    assert torch.equal(losses[0], losses[1])
-    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
-    for g0, g1 in zip(grads[0][2], grads[1][2]):
+    r = [_raw_step(simt_ctx, wl, uv, tgt, small) for small in (False, True)]
+    assert torch.equal(r[0][0], r[1][0])
+    assert torch.equal(r[0][1], r[1][1]) and torch.equal(r[0][2], r[1][2])
+    for g0, g1 in zip(r[0][3], r[1][3]):
         assert (g0 - g1).abs().max().item() <= 1e-6 * g0.abs().max().item()
+
+
+@pytest.mark.parametrize("which", ["mid", "full"])
+def test_tensor_core_and_simt_steps_agree(nb, ctx, simt_ctx, which):
+    """The tensor-core step (pre-gathered samples, split FP16 operands with FP32
+    accumulation) against the FP32 SIMT step on the same kink-free batch: loss
+    and MLP gradients within 1e-5 relative, latent gradients within 1e-5 of
+    their largest magnitude.  The FP64 parity tests above hold each one to the
+    oracle at 1e-4; this bounds the two kernels' difference directly."""
+    from paper_2506_06040_gb300.train import padded
+    wl = _mid_workload(seed=81) if which == "mid" else synth.train_workload(full=True)
+    uv = torch.from_numpy(kink_free(wl, wl.uv(0))).cuda()
+    tgt = padded(torch.from_numpy(wl.target).cuda())
+    tc = _raw_step(ctx, wl, uv, tgt, False)
+    ref = _raw_step(simt_ctx, wl, uv, tgt, False)
+    tol = 1e-5
+    assert abs(tc[0].item() - ref[0].item()) <= tol * abs(ref[0].item())
+    for got, want in ((tc[1], ref[1]), (tc[2], ref[2])):
+        d = (got - want).double()
+        assert d.norm().item() <= tol * want.double().norm().item()
+    for g, w in zip(tc[3], ref[3]):
+        assert (g - w).abs().max().item() <= tol * w.abs().max().item()
 
 
 @pytest.mark.parametrize("C,pad", [(3, False), (12, True), (13, True), (16, False), (5, True)])
