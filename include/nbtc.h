@@ -121,13 +121,16 @@ typedef struct nbtc_context nbtc_context;
  * context owns a 4-byte device status word and nothing else per device.
  * Returns NBTC_ERR_INVALID_ARG for a NULL `ctx`, NBTC_ERR_UNSUPPORTED when the
  * device is not compute capability 10.3, NBTC_ERR_CUDA when CUDA fails.
- * Two environment variables, read here, select kernel shapes for measurement
- * (results are identical either way): NBTC_TC_GROUPS=3 runs the single-material
- * tensor-core decode with 3 warpgroups per CTA instead of 4 (NBTC_TC_GROUPS=2
- * runs the split FP16 form as 2 warpgroups of two tile slots instead of 4 of
- * one), NBTC_FP32_GROUPS=1
- * runs the FP32 wide decode as one 512-thread group per CTA instead of two
- * independent 256-thread groups. */
+ * Environment variables, read here, select kernel variants for measurement
+ * (decode results are bit-identical either way): NBTC_TC_TMEM_A=0 keeps the
+ * MMA A operands of the FP16 tensor-core forms (FP16, FP16_SPLIT, FP32_TC) in
+ * shared memory instead of tensor memory; NBTC_TC_GROUPS=3 runs the
+ * shared-memory-operand FP16 / FP8 decodes with 3 warpgroups per CTA instead of
+ * 4; NBTC_FP32_GROUPS=1 runs the FP32 wide decode as one 512-thread group per
+ * CTA instead of two independent 256-thread groups; NBTC_TRAIN_SIMT=1 runs
+ * every training step on the FP32 SIMT kernel (default: the tensor-core kernel
+ * whenever the workspace holds the gathered samples; results agree to FP32
+ * rounding, not bit for bit). */
 nbtc_status nbtc_create(int device, nbtc_context** ctx);
 
 /* Frees the context (synchronises the device first).  NULL is accepted. */
@@ -430,6 +433,9 @@ typedef struct {
   int64_t frame_uniform_tiles, frame_mixed_tiles, frame_packed_tiles;  /* of the last render */
   float tuned_decode_ms, tuned_render_ms;  /* autotuner's best times (0 = not tuned) */
   int32_t render_warpgroups;                /* tile groups per CTA of the frame decode */
+  int32_t decode_tmem_operands;             /* 1: the decode's MMA A operands live in tensor memory
+                                               (one tile slot per group), 0: in shared memory (two) */
+  int32_t render_tmem_operands;             /* the same for the frame decode */
 } nbtc_batch_info;
 
 #define NBTC_BATCH_AUTOTUNE 1  /* flags: time the candidate configurations at creation */

@@ -69,7 +69,8 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("warpgroups", c_int32), ("chunk_tiles", c_int32), ("tile_w", c_int32), ("tile_h", c_int32),
                 ("decode_tiles", c_int64), ("frame_uniform_tiles", c_int64), ("frame_mixed_tiles", c_int64),
                 ("frame_packed_tiles", c_int64), ("tuned_decode_ms", c_float), ("tuned_render_ms", c_float),
-                ("render_warpgroups", c_int32)]
+                ("render_warpgroups", c_int32), ("decode_tmem_operands", c_int32),
+                ("render_tmem_operands", c_int32)]
 
 
 BATCH_AUTOTUNE = 1

@@ -205,6 +205,7 @@ struct nbtc_batch {
   size_t plist_ints = 0;
   // tuned configuration and graphs
   int W = 3, Wf = 3, chunk = 32, tw = 16, th = 8;  // W: decode warpgroups, Wf: render warpgroups
+  int ta = 0, taf = 0;  // A operands in TMEM (4 warpgroups x 1 slot) for the decode / the frame
   cudaStream_t cap = nullptr;
   cudaGraphExec_t g_decode = nullptr, g_render = nullptr;
   nbtc_batch_info info{};
@@ -249,7 +250,8 @@ static nbtc_status enqueue_decode(nbtc_context* ctx, nbtc_batch* B, cudaStream_t
   p.chunks = B->dchunks;
   p.nchunks_dev = B->dnchunks;
   p.chunk_counter = B->dcounter;
-  return launch_tc_args(ctx, p, B->nhid, kF16, B->W, 2, ctx->sm_count, s);
+  p.tmem_a = B->ta;
+  return launch_tc_args(ctx, p, B->nhid, kF16, B->W, B->ta ? 1 : 2, ctx->sm_count, s);
 }
 
 // Lighting constants of a frame: unit directions and the half vector, in double
@@ -316,7 +318,8 @@ static nbtc_status enqueue_render(nbtc_context* ctx, nbtc_batch* B, cudaStream_t
   p.tile_w = F.tw;
   p.tile_h = F.th;
   p.tiles_x = F.tiles_x;
-  return launch_tc_args(ctx, p, B->nhid, kF16, B->Wf, 2, ctx->sm_count, s);
+  p.tmem_a = B->taf;
+  return launch_tc_args(ctx, p, B->nhid, kF16, B->Wf, B->taf ? 1 : 2, ctx->sm_count, s);
 }
 
 static nbtc_status set_tile_shape(nbtc_batch* B, int tw, int th) {
@@ -559,11 +562,14 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
   // ---- autotune: warpgroups x chunk size (decode); warpgroups x tile shape (frame)
   if (flags & NBTC_BATCH_AUTOTUNE) {
     float best = 1e30f;
-    int bw = B->W, bc = B->chunk;
+    int bw = B->W, bc = B->chunk, bta = B->ta;
+    // candidates: 3 or 4 warpgroups of two slots with shared-memory operands,
+    // or 4 warpgroups of one slot with TMEM operands (coded as W = 5 here)
     if (B->decode_tiles > 0) {
-      for (int W : {3, 4})
+      for (int W : {3, 4, 5})
         for (int c : {8, 32, 128}) {
-          B->W = W;
+          B->W = W == 5 ? 4 : W;
+          B->ta = W == 5;
           NBTC_TRY(set_decode_chunk(B, c, B->cap));
           const float ms = time_ms([&] { return enqueue_decode(ctx, B, B->cap); }, B->cap, 3, st);
           if (st) {
@@ -572,22 +578,25 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
           }
           if (ms < best) {
             best = ms;
-            bw = W;
+            bw = B->W;
+            bta = B->ta;
             bc = c;
           }
         }
       B->W = bw;
+      B->ta = bta;
       NBTC_TRY(set_decode_chunk(B, bc, B->cap));
       B->info.tuned_decode_ms = best;
     }
     if (B->has_frame) {
       float bestf = 1e30f;
-      int fw = B->Wf, ftw = 16, fth = 8;
+      int fw = B->Wf, fta = B->taf, ftw = 16, fth = 8;
       const int shapes[4][2] = {{16, 8}, {32, 4}, {8, 16}, {128, 1}};
-      for (int W : {3, 4})
+      for (int W : {3, 4, 5})
         for (auto& sh : shapes) {
           if (set_tile_shape(B, sh[0], sh[1])) continue;
-          B->Wf = W;
+          B->Wf = W == 5 ? 4 : W;
+          B->taf = W == 5;
           const float ms = time_ms([&] { return enqueue_render(ctx, B, B->cap); }, B->cap, 3, st);
           if (st) {
             free_plan(B);
@@ -595,13 +604,15 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
           }
           if (ms < bestf) {
             bestf = ms;
-            fw = W;
+            fw = B->Wf;
+            fta = B->taf;
             ftw = sh[0];
             fth = sh[1];
           }
         }
       NBTC_TRY(set_tile_shape(B, ftw, fth));
       B->Wf = fw;
+      B->taf = fta;
       B->info.tuned_render_ms = bestf;
     }
   }
@@ -611,6 +622,8 @@ nbtc_status nbtc_batch_create(nbtc_context* ctx, const nbtc_batch_material* mats
 #undef NBTC_TRY
   B->info.warpgroups = B->W;
   B->info.render_warpgroups = B->Wf;
+  B->info.decode_tmem_operands = B->ta;
+  B->info.render_tmem_operands = B->taf;
   B->info.chunk_tiles = B->chunk;
   B->info.tile_w = B->tw;
   B->info.tile_h = B->th;

@@ -158,7 +158,8 @@ nbtc_status nbtc_create(int device, nbtc_context** out) {
   nbtc_context* ctx = new nbtc_context();
   ctx->device = device;
   ctx->sm_count = prop.multiProcessorCount;
-  if (const char* e = getenv("NBTC_TC_GROUPS")) ctx->tc_groups = atoi(e) == 3 ? 3 : atoi(e) == 2 ? 2 : 4;
+  if (const char* e = getenv("NBTC_TC_GROUPS")) ctx->tc_groups = atoi(e) == 3 ? 3 : 4;
+  if (const char* e = getenv("NBTC_TC_TMEM_A")) ctx->tc_tmem_a = atoi(e) == 0 ? 0 : 1;
   if (const char* e = getenv("NBTC_FP32_GROUPS")) ctx->fp32_groups = atoi(e) == 1 ? 1 : 2;
   if (const char* e = getenv("NBTC_TRAIN_SIMT")) ctx->train_tc = atoi(e) == 1 ? 0 : 1;
   if ((st = cuda_check(cudaMalloc(&ctx->status_dev, sizeof(int)), "cudaMalloc(status)"))) {

@@ -152,6 +152,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
         "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
 }
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 
@@ -188,6 +193,21 @@ __device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint3
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d),
       "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+
+// A operand in TMEM (row m in lane m, K packed along the columns: two 16-bit
+// or four 8-bit elements per 32-bit column), B in shared memory.
+__device__ __forceinline__ void mma_f16_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+      "r"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_f8_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+      "r"(a), "l"(b), "r"(id), "r"(acc)
       : "memory");
 }
 
@@ -244,8 +264,13 @@ __device__ __forceinline__ float2 f16x2_to_float2(uint32_t v) {
 //  FP16:  hi = RN16(v), lo = RN16(v - hi) (v - hi is exact in FP32)
 __device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
   hi = cvt_f16x2(a, b);
-  const float2 h = f16x2_to_float2(hi);
-  lo = cvt_f16x2(a - h.x, b - h.y);
+  // a - hi(a) with one mixed-precision FMA each (FP16 hi times -1 plus FP32 a):
+  // the difference is exact in FP32, so this equals the plain FP32 subtraction
+  float ra, rb;
+  asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n fma.rn.f32.f16 %0, l, %3, %4;\n fma.rn.f32.f16 %1, h, %3, %5;\n}"
+      : "=f"(ra), "=f"(rb)
+      : "r"(hi), "h"((unsigned short)0xBC00u), "f"(a), "f"(b));
+  lo = cvt_f16x2(ra, rb);
 }
 __device__ __forceinline__ void split_relu_f16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
   split_f16x2(fmaxf(a, 0.f), fmaxf(b, 0.f), hi, lo);

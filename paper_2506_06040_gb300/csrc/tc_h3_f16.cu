@@ -4,6 +4,10 @@
 namespace nbtc {
 
 nbtc_status launch_tc_h3_f16(const TcArgs& p, int W, int slots, int grid, cudaStream_t s) {
+  if (p.tmem_a) {  // A operands in TMEM: 4 warpgroups x 1 slot
+    if (W == 4 && slots == 1) return launch_tc_w<3, kF16, 4, kModeSingle, 1, true>(p, grid, s);
+    return fail(NBTC_ERR_UNSUPPORTED, "TMEM operands: 4 warpgroups x 1 slot");
+  }
   if (slots != 2) return fail(NBTC_ERR_UNSUPPORTED, "this form runs two tile slots per warpgroup");
   return W == 3 ? launch_tc_w<3, kF16, 3, kModeSingle, 2>(p, grid, s) : launch_tc_w<3, kF16, 4, kModeSingle, 2>(p, grid, s);
 }

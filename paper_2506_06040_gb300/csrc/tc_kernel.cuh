@@ -75,7 +75,7 @@ struct TcSmem {
   int total;
 };
 
-__host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W, int NSL) {
+__host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W, int NSL, bool ta = false) {
   TcSmem s;
   const int NS = W * NSL;
   s.image = (L.bytes() + 1023) & ~1023;
@@ -86,13 +86,13 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W, int NSL) {
     s.ah = 0;
     s.ah_lo = 16384;
     s.colbuf = 16384;
-    s.slot = 32768;
+    s.slot = ta ? 0 : 32768;  // A operands in TMEM: no slot buffers
   } else {
     s.a0 = 0;
     s.ah = 4096;
     s.ah_lo = 8192;   // FP8 split: 128 x 64 E4M3 hi, then lo
     s.colbuf = 4096;
-    s.slot = 4096 + 16384;
+    s.slot = ta ? 0 : 4096 + 16384;  // A operands in TMEM: no slot buffers
   }
   s.stage = s.slots + NS * s.slot;
   s.bars = s.stage + W * 4 * stage_bytes(L.form);
@@ -120,20 +120,32 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W, int NSL) {
 // always complete and the kernel always terminates.
 // MODE kModeSingle: one material whose views are kernel parameters; kModeBatch:
 // chunks of many materials (and frame tiles) whose views live in shared memory.
-template <int NHID, int FORM, int W, int MODE, int NSL>
+template <int NHID, int FORM, int W, int MODE, int NSL, bool TA = false>
 __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   constexpr TcLayout L{NHID, FORM};
+  static_assert(!TA || FORM == kF16 || FORM == kF16Split || FORM == kF32Split, "TMEM A operands: FP16 forms");
   constexpr bool FP8 = FORM == kF8 || FORM == kF8Split;
   constexpr bool F16S = FORM == kF16Split || FORM == kF32Split;  // split FP16 operands
   constexpr bool SPLIT = F16S || FORM == kF8Split;
   constexpr bool OUT32 = FORM == kF32Split;                      // FP32 output
   constexpr int kSlots = NSL;
   constexpr int NS = W * kSlots;
-  constexpr uint32_t kTmemCols = NS * kHid <= 256 ? 256 : 512;
-  static_assert(NS * kHid <= 512, "TMEM holds at most 512 columns");
+  // TMEM per slot: the accumulator (64 columns); with TA a 128-column slot
+  // holds the accumulator, then the slot's A operand: 64 FP16 = 32 columns
+  // (split forms: the hi tile, then the lo tile)
+  constexpr uint32_t kSlotCols = TA ? 2 * kHid : kHid;
+  constexpr uint32_t kAcol = kHid;                  // TA: A (hi) columns within a slot
+  constexpr uint32_t kAlo = kHid + kHid / 2;        // TA, split forms: lo columns
+  // TA, FP16: the bias products' A (ones) as an 8-column TMEM tile in the last
+  // slot's spare columns; the split forms read the shared-memory ones tile
+  constexpr bool kOnesT = TA && FORM == kF16;
+  constexpr uint32_t kOnesCol = (NS - 1) * kSlotCols + kAlo;
+  constexpr uint32_t kUsedCols = NS * kSlotCols;
+  constexpr uint32_t kTmemCols = kUsedCols <= 256 ? 256 : 512;
+  static_assert(kUsedCols <= 512, "TMEM holds at most 512 columns");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const TcSmem S = tc_smem(L, W, NSL);
+  const TcSmem S = tc_smem(L, W, NSL, TA);
   const uint32_t sbase = smem_u32(smem);
   const int tid = threadIdx.x;
   const int warp = tid / 32, lane = tid % 32;
@@ -167,6 +179,18 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  if constexpr (kOnesT) {
+    // element k = 0 of every row is 1.0 (FP16), the rest 0; warp w < 4 writes
+    // the rows of its lane quarter
+    if (warp < 4) {
+      const uint32_t ones[8] = {0x3C00u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+      tmem_st8(tmem_base + kOnesCol + ((uint32_t)(32 * warp) << 16), ones);
+      tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
   bool failed = false;
   uint32_t wph = 0;  // phase of the weight barrier
 
@@ -264,9 +288,41 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
             named_bar_sync(bar_a(q), kTile + 32);
             if (lane == 0) {
               tc_fence_after();
-              const uint32_t d = tmem_base + (uint32_t)(q * kHid);
+              const uint32_t d = tmem_base + (uint32_t)q * kSlotCols;
               const uint32_t slot = sbase + S.slots + q * S.slot;
-              if (l == 0) {
+              if constexpr (TA) {
+                // A from TMEM (K = 16: 8 columns per product), B from shared
+                // memory; the bias product's A is the ones tile in shared memory
+                const uint32_t ah = d + kAcol, al = d + kAlo;
+                if (l == 0) {
+                  if constexpr (F16S) {
+                    // A0: hi [x 1 000] in 8 columns at kAcol, lo [x 1 000] at kAlo
+                    mma_f16_ts(d, ah, dsc(hi_w1, lo_w1), ID_HID, 0);       // hi x . hi W + hi b
+                    mma_f16_ts(d, al, dsc(hi_w1, lo_w1 + 16), ID_HID, 1);  // lo x . hi W + lo b
+                    mma_f16_ts(d, ah, dsc(hi_w1, lo_w1 + 32), ID_HID, 1);  // hi x . lo W
+                  } else {
+                    mma_f16_ts(d, ah, dsc(hi_w1, lo_w1), ID_HID, 0);       // [x 1 0 0 0] . [W b 0 0 0]
+                  }
+                } else {
+                  const bool last = l == NHID;
+                  const uint32_t id = last ? ID_OUT : ID_HID;
+                  const uint32_t lo_b = lo(sbase + (last ? L.off_wo() : L.off_wh(l - 1)), 16);
+                  const uint32_t lo_bt = lo(sbase + (last ? L.off_bto() : L.off_bth(l - 1)), 128);
+                  const uint32_t db = (uint32_t)(last ? L.wo_part() : L.wh_part()) >> 4;  // lo W, 16-byte units
+                  if constexpr (kOnesT)
+                    mma_f16_ts(d, tmem_base + kOnesCol, dsc(hi_int, lo_bt), id, 0);
+                  else
+                    mma_f16(d, dsc(hi_int, lo_ones), dsc(hi_int, lo_bt), id, 0);
+#pragma unroll
+                  for (int kk = 0; kk < 4; ++kk) {
+                    mma_f16_ts(d, ah + 8 * kk, dsc(hi_w, lo_b + 2 * kk), id, 1);
+                    if constexpr (F16S) {
+                      mma_f16_ts(d, al + 8 * kk, dsc(hi_w, lo_b + 2 * kk), id, 1);
+                      mma_f16_ts(d, ah + 8 * kk, dsc(hi_w, lo_b + db + 2 * kk), id, 1);
+                    }
+                  }
+                }
+              } else if (l == 0) {
                 // K chunks of 32 bytes (16 FP16 / 32 E4M3), 256 bytes apart in
                 // the no-swizzle layout
                 const uint32_t la = lo(slot + S.a0, 128);
@@ -360,7 +416,28 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
           else
             trilinear_features(work.m, uv.x, uv.y, __ldg(p.flod + pq), f);
         }
-        if constexpr (FORM == kF16) {
+        if constexpr (TA) {
+          const uint32_t ta = tmem_base + (uint32_t)q * kSlotCols + lane_off;
+          if constexpr (F16S) {
+            uint32_t h[8], r[8];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) split_f16x2(f[2 * i], f[2 * i + 1], h[i], r[i]);
+            h[6] = r[6] = 0x3C00u;  // k = 12: 1.0 for hi(b) / lo(b)
+            h[7] = r[7] = 0u;
+            tmem_st8(ta + kAcol, h);
+            tmem_st8(ta + kAlo, r);
+          } else {
+            const uint32_t h[8] = {cvt_f16x2(f[0], f[1]), cvt_f16x2(f[2], f[3]),  cvt_f16x2(f[4], f[5]),
+                                   cvt_f16x2(f[6], f[7]), cvt_f16x2(f[8], f[9]),  cvt_f16x2(f[10], f[11]),
+                                   0x3C00u /* k = 12: 1.0 for the bias */, 0u};
+            tmem_st8(ta + kAcol, h);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          named_bar_arrive(bar_a(q), kTile + 32);
+          return;
+        } else if constexpr (FORM == kF16) {
           sts128(a0 + off_interleave(gt, 0), cvt_f16x2(f[0], f[1]), cvt_f16x2(f[2], f[3]), cvt_f16x2(f[4], f[5]),
                  cvt_f16x2(f[6], f[7]));
           sts128(a0 + off_interleave(gt, 16), cvt_f16x2(f[8], f[9]), cvt_f16x2(f[10], f[11]),
@@ -406,7 +483,32 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       // narrow -> Ah, then A-ready
       auto hidden_epilogue = [&](int s, int l) {
         const int q = wg * kSlots + s;
-        const uint32_t taddr = tmem_base + (uint32_t)(q * kHid) + lane_off;
+        const uint32_t taddr = tmem_base + (uint32_t)q * kSlotCols + lane_off;
+        if constexpr (TA) {
+          // ReLU -> FP16 pairs (split: hi and lo pairs) -> the slot's A columns
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            uint32_t r[32], h[16];
+            tmem_ld32_wait(taddr + 32 * part, r);
+            if constexpr (F16S) {
+              uint32_t lw[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                split_relu_f16x2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]), h[j], lw[j]);
+              tmem_st16(taddr + kAlo + 16 * part, lw);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                h[j] = cvt_relu_f16x2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+            }
+            tmem_st16(taddr + kAcol + 16 * part, h);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          named_bar_arrive(bar_a(q), kTile + 32);
+          return;
+        }
         const uint32_t ah = sbase + S.slots + q * S.slot + S.ah;
         const float alp = alpha[l];
         const float* b = bias + l * kHid;
@@ -480,7 +582,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       // output epilogue of slot s, tile T: accumulator -> FP16 -> global
       auto output_epilogue = [&](int s, int64_t T) {
         const int q = wg * kSlots + s;
-        const uint32_t taddr = tmem_base + (uint32_t)(q * kHid) + lane_off;
+        const uint32_t taddr = tmem_base + (uint32_t)q * kSlotCols + lane_off;
         uint32_t r[16];
         tmem_ld16_wait(taddr, r);
         tc_fence_before();
@@ -619,10 +721,10 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
 }
 
 
-template <int NHID, int FORM, int W, int MODE, int NSL>
+template <int NHID, int FORM, int W, int MODE, int NSL, bool TA = false>
 nbtc_status launch_tc_w(const TcArgs& p, int grid, cudaStream_t s) {
-  const TcSmem S = tc_smem(TcLayout{NHID, FORM}, W, NSL);
-  auto kern = k_decode_tc<NHID, FORM, W, MODE, NSL>;
+  const TcSmem S = tc_smem(TcLayout{NHID, FORM}, W, NSL, TA);
+  auto kern = k_decode_tc<NHID, FORM, W, MODE, NSL, TA>;
   nbtc_status st =
       cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S.total), "smem attribute");
   if (st) return st;

@@ -106,21 +106,32 @@ def test_split_empty_decode(nb, ctx):
         assert y.shape == (0, 9)
 
 
-def test_fp16_split_shapes_agree(nb, ctx):
-    """The FP16 split form runs 4 warpgroups of one tile slot (default) or 2 of two
-    (NBTC_TC_GROUPS=2): the same arithmetic per tile, bit-identical outputs."""
-    wl = synth.small_decode_workload(1024, [12, 64, 64, 64, 9], seed=440)
-    mat, packed, _ = _prepare(nb, ctx, wl, "fp16s", None)
-    a = nb.decode(ctx, mat, nb.FP16_SPLIT, packed, grid=(1024, 200))
-    os.environ["NBTC_TC_GROUPS"] = "2"
+@pytest.mark.parametrize("form", ["fp16", "fp16s", "fp32tc"])
+def test_tmem_and_shared_memory_operands_agree(nb, ctx, form):
+    """The FP16 tensor-core forms keep their MMA A operands in tensor memory
+    (default) or in shared memory (NBTC_TC_TMEM_A=0): the same products in the
+    same order, so bit-identical outputs -- on a ragged grid (1024 x 200 plus a
+    partial last tile) and a uv list."""
+    dims = [12, 64, 64, 9] if form == "fp32tc" else [12, 64, 64, 64, 9]
+    wl = synth.small_decode_workload(1024, dims, seed=440)
+    code = {"fp16": nb.FP16, "fp16s": nb.FP16_SPLIT, "fp32tc": nb.FP32_TC}[form]
+    os.environ["NBTC_TC_TMEM_A"] = "0"
     try:
         c2 = nb.Context(0)
     finally:
-        del os.environ["NBTC_TC_GROUPS"]
-    b = nb.decode(c2, mat, nb.FP16_SPLIT, packed, grid=(1024, 200))
-    c2.sync()
-    ctx.sync()
-    assert torch.equal(a.view(torch.int16), b.view(torch.int16))
+        del os.environ["NBTC_TC_TMEM_A"]
+    mat = nb.Material.from_synth(wl.material)
+    uv = torch.from_numpy(synth.Rng(441, 1).uniform(2 * 30011, -0.25, 1.25).reshape(-1, 2).astype(np.float32)).cuda()
+    for c in (ctx, c2):
+        c.sync()
+    outs = []
+    for c in (ctx, c2):
+        packed = nb.pack_mlp(c, mat, code)
+        outs.append((nb.decode(c, mat, code, packed, grid=(1024, 200)), nb.decode(c, mat, code, packed, uv=uv)))
+        c.sync()
+    iv = torch.int32 if form == "fp32tc" else torch.int16
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a.view(iv), b.view(iv))
     c2.close()
 
 
