@@ -272,8 +272,19 @@ __device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint
       : "r"(hi), "h"((unsigned short)0xBC00u), "f"(a), "f"(b));
   lo = cvt_f16x2(ra, rb);
 }
+// split of (relu a, relu b) without forming relu in FP32: hi = RN16(relu v) by
+// the converting ReLU; for v < 0, hi = 0 and the residual v - hi = v rounds to
+// a negative (or zero) lo, which max(lo, -hi) = max(lo, -0) zeroes; for v >= 0,
+// |lo| <= |hi| (hi != 0) or lo = 0 (hi = 0), so max(lo, -hi) = lo.  Same
+// values as split_f16x2(relu a, relu b) (a zero lo may carry either sign).
 __device__ __forceinline__ void split_relu_f16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  split_f16x2(fmaxf(a, 0.f), fmaxf(b, 0.f), hi, lo);
+  hi = cvt_relu_f16x2(a, b);
+  float ra, rb;
+  asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n fma.rn.f32.f16 %0, l, %3, %4;\n fma.rn.f32.f16 %1, h, %3, %5;\n}"
+      : "=f"(ra), "=f"(rb)
+      : "r"(hi), "h"((unsigned short)0xBC00u), "f"(a), "f"(b));
+  const uint32_t r = cvt_f16x2(ra, rb);
+  asm("max.f16x2 %0, %1, %2;" : "=r"(lo) : "r"(r), "r"(hi ^ 0x80008000u));
 }
 //  E4M3 (of an FP16 pair v16): hi = E4M3(v16), lo = E4M3(v16 - hi); the
 //  residual of rounding an FP16 value to E4M3 is itself an FP16 value, so the

@@ -150,10 +150,12 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   const int tid = threadIdx.x;
   const int warp = tid / 32, lane = tid % 32;
   const uint32_t dbar0 = sbase + S.bars, wbar = dbar0 + NS * 8;
-  // named barriers: 0 = __syncthreads, 1 + W + q = A-ready of slot q (1 .. W
-  // unused: the feature stage shares latent columns within a warp)
+  // named barriers: 0 = __syncthreads, 1 + W + q = A-ready of slot q; with TA
+  // (one slot per warpgroup) 1 + q = D-ready of slot q
   static_assert(1 + W + NS <= 16, "named barrier ids");
+  static_assert(!TA || NS <= W, "TMEM operands: one slot per warpgroup");
   auto bar_a = [](int q) { return 1 + W + q; };
+  auto bar_d = [](int q) { return 1 + q; };
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S.tslot);
   TcWork& work = *reinterpret_cast<TcWork*>(smem + S.work);
   int* status = p.d.status;
@@ -371,6 +373,19 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
               mma_commit(dbar0 + q * 8);
             }
             __syncwarp();  // converged before the next (aligned) barrier
+            if constexpr (TA) {
+              // this warp waits for the layer's products (bounded) and then
+              // releases the warpgroup through a hardware barrier, so the
+              // warpgroup's 128 threads sleep instead of polling the mbarrier
+              if (!mbar_wait_bounded(dbar0 + q * 8, dph[s], p.budget)) {
+                failed = true;
+                mbar_wait_bounded(dbar0 + q * 8, dph[s], kDrainBudget);
+              }
+              dph[s] ^= 1u;
+              tc_fence_before();
+              __syncwarp();
+              named_bar_arrive(bar_d(q), kTile + 32);
+            }
           }
         }
       }
@@ -681,11 +696,15 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
             // past the budget: record the timeout, then keep waiting (fixed budget)
             // so the warpgroup never runs ahead of its MMA warp -- running ahead
             // would arrive twice on one A-ready named barrier before it completes
-            if (!mbar_wait_bounded(dbar0 + q * 8, dph[s], p.budget)) {
-              failed = true;
-              mbar_wait_bounded(dbar0 + q * 8, dph[s], kDrainBudget);
+            if constexpr (TA) {
+              named_bar_sync(bar_d(q), kTile + 32);  // the MMA warp saw the products complete
+            } else {
+              if (!mbar_wait_bounded(dbar0 + q * 8, dph[s], p.budget)) {
+                failed = true;
+                mbar_wait_bounded(dbar0 + q * 8, dph[s], kDrainBudget);
+              }
+              dph[s] ^= 1u;
             }
-            dph[s] ^= 1u;
             failed = __any_sync(0xffffffffu, failed);  // one failure state per warp
             tc_fence_after();
             if (l < NHID) {
