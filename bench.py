@@ -290,6 +290,11 @@ MMA_FLOP = {"fp16_tc": 2 * (16 * 64 + 2 * (16 * 64 + 64 * 64) + 16 * 16 + 64 * 1
             "fp16_split_tc": 2 * (3 * 16 * 64 + 2 * (16 * 64 + 3 * 64 * 64) + 16 * 16 + 3 * 64 * 16),
             "fp8_split_tc": 2 * (2 * 32 * 64 + 2 * 3 * 64 * 64 + 3 * 64 * 16)}
 BOUNDS = {"fp16_tc": 2e-3, "fp8_tc": 2e-2, "fp16_split_tc": 2e-3, "fp8_split_tc": 2e-2}
+# MMA FLOP the tensor-core training kernel executes per sample: per 128-sample
+# tile, forward 4 + 13 (N = 64) + 13 (N = 16) products, backward 3 + 12 (N = 64)
+# + 12 (N = 16), weight gradients 24 + 24 + 16 + 24 products at M = 64
+TRAIN_MMA_FLOP_PER_SAMPLE = (2 * 128 * 64 * 16 * (4 + 13 + 3 + 12) + 2 * 128 * 16 * 16 * (13 + 12) +
+                             2 * 64 * 16 * 16 * (24 + 16 + 24) + 2 * 64 * 64 * 16 * 24) // 128
 
 
 def run_forms(args, nb, ctx, stream, flush, peaks, sm_count, ffma, form_ref) -> dict:
@@ -469,8 +474,22 @@ def run_train(args, nb, ctx, stream, flush, sm_count, peaks, ffma) -> dict:
                     max(3, args.steps // 2), args.warmup, flush, stream)
     ms = statistics.mean(t)
     flop = 32640 * wl.batch
-    peak = ffma["tflops"]
     ctx.sync(stream)
+    # the same step on the FP32 SIMT training kernel (a context created with
+    # NBTC_TRAIN_SIMT=1), against the measured FFMA peak
+    os.environ["NBTC_TRAIN_SIMT"] = "1"
+    try:
+        sctx = nb.Context(torch.cuda.current_device())
+    finally:
+        del os.environ["NBTC_TRAIN_SIMT"]
+    smodel = ContinuousModel.from_synth(wl)
+    ts_ = _time_steps(lambda: smodel.train_step(sctx, uvs[next(it) % 4], tgt, stream=stream),
+                      max(3, args.steps // 2), args.warmup, flush, stream)
+    ms_simt = statistics.mean(ts_)
+    sctx.sync(stream)
+    sctx.close()
+    del smodel
+    tc_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
     # the step's L2-atomic co-bound: its latent-gradient scatter alone (same
     # atomics, same addresses), timed the same way
     import ctypes
@@ -484,10 +503,20 @@ def run_train(args, nb, ctx, stream, flush, sm_count, peaks, ffma) -> dict:
     ctx.sync(stream)
     res = {"workload": wl.name, "steps_per_s": 1e3 / ms, "samples_per_s": wl.batch * 1e3 / ms, "ms_per_step": ms,
            "kernels_per_step": 5, "layout": "latents [h][w][4], target [h][w][12] (padding channels unused)",
-           "roofline": {"bound": "alu", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                        "frac": flop / (ms * 1e-3) / 1e12 / peak, "traffic": _profiled_traffic("k_train_batch2p20"),
-                        "peak_source": "measured FFMA probe",
-                        "note": "whole step (forward, backward, reduction, Adam) against the FP32 FFMA peak"},
+           "kernel": "k_train_tc (split FP16 operands on tcgen05, FP32 accumulation)",
+           "roofline": {"bound": "tensor", "achieved": flop / (ms * 1e-3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+                        "frac": flop / (ms * 1e-3) / 1e12 / tc_peak, "traffic": _profiled_traffic("k_train_tc_batch2p20"),
+                        "peak_source": "measured bf16 dense, sustained (a kernel inside a multi-kernel step)",
+                        "executed_mma_flop_per_sample": TRAIN_MMA_FLOP_PER_SAMPLE,
+                        "executed_frac": TRAIN_MMA_FLOP_PER_SAMPLE * wl.batch / (ms * 1e-3) / 1e12 / tc_peak,
+                        "note": "whole step (gather, forward, backward, reduction, Adam): 32,640 FP32-equivalent "
+                                "FLOP per sample; the split operands execute 119,296 MMA FLOP per sample"},
+           "simt_step": {"ms_per_step": ms_simt, "steps_per_s": 1e3 / ms_simt,
+                         "roofline": {"bound": "alu", "achieved": flop / (ms_simt * 1e-3) / 1e12,
+                                      "peak": ffma["tflops"], "unit": "TFLOP/s",
+                                      "frac": flop / (ms_simt * 1e-3) / 1e12 / ffma["tflops"],
+                                      "traffic": _profiled_traffic("k_train_batch2p20"),
+                                      "peak_source": "measured FFMA probe"}},
            "l2_atomics": {"vector_atomics_per_step": n_atomics, "scatter_alone_ms": ms_sc,
                           "share_of_step": ms_sc / ms, "atomics_per_s": n_atomics / (ms_sc * 1e-3),
                           "note": "nbtc_probe_scatter: the step's 16 latent-gradient vector atomics per sample at the "
@@ -545,11 +574,25 @@ def run_batch(args, nb, ctx, stream, flush) -> dict:
     ctx.sync(stream)
     lplan.close()
     pixels = bw.frame_w * bw.frame_h
+    # probes per pixel of the anisotropic frame (the kernel's rule in FP32:
+    # N = min(ceil(Pmax / Pmin), 16)) and the frame time per probe
+    d = np.ascontiguousarray(bw.duv, dtype=np.float32)
+    p_x = np.sqrt(d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1])
+    p_y = np.sqrt(d[..., 2] * d[..., 2] + d[..., 3] * d[..., 3])
+    pmax, pmin = np.maximum(p_x, p_y), np.minimum(p_x, p_y)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        nprobe = np.where(pmax > 0, np.where(pmin > 0, np.minimum(np.ceil(pmax / pmin), 16), 16), 1).astype(np.int64)
+    hist = np.bincount(nprobe.ravel(), minlength=17)[1:17]
+    mean_probes = float(nprobe.mean())
+    aniso = {"probe_histogram_1_to_16": [int(x) for x in hist], "mean_probes": mean_probes,
+             "bc1_texel_decodes_per_pixel": 32.0 * mean_probes,
+             "ms_per_probe_vs_trilinear": statistics.mean(ta) / mean_probes / statistics.mean(tr)}
     return {"workload": bw.name, "materials": len(bw.materials), "decode_texels": texels,
             "decode_gtexel_s": texels / statistics.mean(td) / 1e6, "decode_ms": statistics.mean(td),
             "frame": f"{bw.frame_w}x{bw.frame_h}", "frame_ms": statistics.mean(tr),
             "frame_gpx_s": pixels / statistics.mean(tr) / 1e6, "plan": info,
             "frame_aniso16_ms": statistics.mean(ta), "frame_aniso16_gpx_s": pixels / statistics.mean(ta) / 1e6,
+            "frame_aniso16_probes": aniso,
             "frame_lit_ms": statistics.mean(tl), "frame_lit_gpx_s": pixels / statistics.mean(tl) / 1e6}
 
 

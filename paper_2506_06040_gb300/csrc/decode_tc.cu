@@ -258,13 +258,13 @@ nbtc_status launch_tc_args(nbtc_context* ctx, const TcArgs& p, int nhid, int for
   return single[form][nhid - 1](p, W, slots, grid, s);
 }
 
-// Warpgroups and tile slots per CTA of a form.  The FP16 forms keep their MMA
-// A operands in TMEM (default): a slot is 128 TMEM columns (accumulator + A),
-// so 4 warpgroups x 1 slot.  With shared-memory operands (context setting) the
+// Warpgroups and tile slots per CTA of a form.  The forms keep their MMA A
+// operands in TMEM (default): a slot is 128 TMEM columns (accumulator + A), so
+// 4 warpgroups x 1 slot.  With shared-memory operands (context setting) the
 // split-FP16 forms, whose two A tiles per slot fill shared memory, run 4 x 1;
 // the others two slots of 3 or 4 warpgroups (context setting).
 static void tc_shape_of(const nbtc_context* ctx, int form, int& W, int& slots) {
-  const bool ta = (form == kF16 || form == kF16Split || form == kF32Split) && ctx->tc_tmem_a;
+  const bool ta = ctx->tc_tmem_a != 0;
   if (ta || form == kF16Split || form == kF32Split) {
     W = 4;
     slots = 1;
@@ -297,7 +297,7 @@ nbtc_status launch_decode_tc(nbtc_context* ctx, const DecodeArgs& a, const nbtc_
   if (p.tiles >= (int64_t)1 << 31) return fail(NBTC_ERR_UNSUPPORTED, "more than 2^31 tiles");
   int W, slots;
   tc_shape_of(ctx, form, W, slots);
-  p.tmem_a = (form == kF16 || form == kF16Split || form == kF32Split) && ctx->tc_tmem_a ? 1 : 0;
+  p.tmem_a = ctx->tc_tmem_a ? 1 : 0;
   int64_t grid = (p.tiles + W * slots - 1) / (W * slots);
   if (grid > ctx->sm_count) grid = ctx->sm_count;
   p.per_cta = (p.tiles + grid - 1) / grid;

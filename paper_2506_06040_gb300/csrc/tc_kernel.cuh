@@ -123,7 +123,6 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W, int NSL, boo
 template <int NHID, int FORM, int W, int MODE, int NSL, bool TA = false>
 __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   constexpr TcLayout L{NHID, FORM};
-  static_assert(!TA || FORM == kF16 || FORM == kF16Split || FORM == kF32Split, "TMEM A operands: FP16 forms");
   constexpr bool FP8 = FORM == kF8 || FORM == kF8Split;
   constexpr bool F16S = FORM == kF16Split || FORM == kF32Split;  // split FP16 operands
   constexpr bool SPLIT = F16S || FORM == kF8Split;
@@ -135,7 +134,8 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   // (split forms: the hi tile, then the lo tile)
   constexpr uint32_t kSlotCols = TA ? 2 * kHid : kHid;
   constexpr uint32_t kAcol = kHid;                  // TA: A (hi) columns within a slot
-  constexpr uint32_t kAlo = kHid + kHid / 2;        // TA, split forms: lo columns
+  // A of a hidden layer: 64 FP16 (32 columns) or 64 E4M3 (16 columns) per part
+  constexpr uint32_t kAlo = kHid + (FP8 ? kHid / 4 : kHid / 2);  // TA, split forms: lo columns
   // TA, FP16: the bias products' A (ones) as an 8-column TMEM tile in the last
   // slot's spare columns; the split forms read the shared-memory ones tile
   constexpr bool kOnesT = TA && FORM == kF16;
@@ -293,10 +293,32 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
               const uint32_t d = tmem_base + (uint32_t)q * kSlotCols;
               const uint32_t slot = sbase + S.slots + q * S.slot;
               if constexpr (TA) {
-                // A from TMEM (K = 16: 8 columns per product), B from shared
-                // memory; the bias product's A is the ones tile in shared memory
+                // A from TMEM (8 columns per product: K = 16 FP16 or 32 E4M3),
+                // B from shared memory; the FP16 bias product's A is the ones tile
                 const uint32_t ah = d + kAcol, al = d + kAlo;
-                if (l == 0) {
+                if constexpr (FP8) {
+                  if (l == 0) {
+                    if constexpr (SPLIT) {
+                      mma_f8_ts(d, ah, dsc(hi_w1, lo_w1), ID_HID, 0);       // [hi x | lo x] . hi W
+                      mma_f8_ts(d, ah, dsc(hi_w1, lo_w1 + 16), ID_HID, 1);  // [hi x | lo x] . [lo W | 0]
+                    } else {
+                      mma_f8_ts(d, ah, dsc(hi_w1, lo_w1), ID_HID, 0);
+                    }
+                  } else {
+                    const bool last = l == NHID;
+                    const uint32_t id = last ? ID_OUT : ID_HID;
+                    const uint32_t lo_b = lo(sbase + (last ? L.off_wo() : L.off_wh(l - 1)), 16);
+                    const uint32_t db = (uint32_t)(last ? L.wo_part() : L.wh_part()) >> 4;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                      mma_f8_ts(d, ah + 8 * kk, dsc(hi_w, lo_b + 2 * kk), id, kk > 0);
+                      if constexpr (SPLIT) {
+                        mma_f8_ts(d, al + 8 * kk, dsc(hi_w, lo_b + 2 * kk), id, 1);
+                        mma_f8_ts(d, ah + 8 * kk, dsc(hi_w, lo_b + db + 2 * kk), id, 1);
+                      }
+                    }
+                  }
+                } else if (l == 0) {
                   if constexpr (F16S) {
                     // A0: hi [x 1 000] in 8 columns at kAcol, lo [x 1 000] at kAlo
                     mma_f16_ts(d, ah, dsc(hi_w1, lo_w1), ID_HID, 0);       // hi x . hi W + hi b
@@ -433,7 +455,25 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
         }
         if constexpr (TA) {
           const uint32_t ta = tmem_base + (uint32_t)q * kSlotCols + lane_off;
-          if constexpr (F16S) {
+          if constexpr (FP8) {
+            // A0 row of 32 E4M3: [x(12) 0 x 20], split: [hi x(12) 0000 | lo x(12) 0000]
+            const float is = alpha[NHID + 1];  // 1 / input scale
+            uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              if constexpr (SPLIT) {
+                uint16_t h0, r0, h1, r1;
+                split_e4m3x2(cvt_f16x2(f[4 * i] * is, f[4 * i + 1] * is), h0, r0);
+                split_e4m3x2(cvt_f16x2(f[4 * i + 2] * is, f[4 * i + 3] * is), h1, r1);
+                w[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                w[4 + i] = (uint32_t)r0 | ((uint32_t)r1 << 16);
+              } else {
+                w[i] = (uint32_t)cvt_e4m3x2(f[4 * i] * is, f[4 * i + 1] * is) |
+                       ((uint32_t)cvt_e4m3x2(f[4 * i + 2] * is, f[4 * i + 3] * is) << 16);
+              }
+            }
+            tmem_st8(ta + kAcol, w);
+          } else if constexpr (F16S) {
             uint32_t h[8], r[8];
 #pragma unroll
             for (int i = 0; i < 6; ++i) split_f16x2(f[2 * i], f[2 * i + 1], h[i], r[i]);
@@ -499,7 +539,42 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       auto hidden_epilogue = [&](int s, int l) {
         const int q = wg * kSlots + s;
         const uint32_t taddr = tmem_base + (uint32_t)q * kSlotCols + lane_off;
-        if constexpr (TA) {
+        if constexpr (TA && FP8) {
+          // scale and bias (packed FP32 FMAs), ReLU -> E4M3 quads (split: hi and
+          // lo quads) -> the slot's A columns (8 per 32 activations)
+          const float alp = alpha[l];
+          const float* b = bias + l * kHid;
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            uint32_t r[32], w[8], wl[8];
+            tmem_ld32_wait(taddr + 32 * part, r);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const int j = 4 * c;
+              const float4 bb = *reinterpret_cast<const float4*>(b + 32 * part + j);
+              const float2 v0 = __ffma2_rn(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
+                                           make_float2(alp, alp), make_float2(bb.x, bb.y));
+              const float2 v1 = __ffma2_rn(make_float2(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])),
+                                           make_float2(alp, alp), make_float2(bb.z, bb.w));
+              if constexpr (SPLIT) {
+                uint16_t h0, r0, h1, r1;
+                split_e4m3x2(cvt_relu_f16x2(v0.x, v0.y), h0, r0);
+                split_e4m3x2(cvt_relu_f16x2(v1.x, v1.y), h1, r1);
+                w[c] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                wl[c] = (uint32_t)r0 | ((uint32_t)r1 << 16);
+              } else {
+                w[c] = (uint32_t)cvt_relu_e4m3x2(v0.x, v0.y) | ((uint32_t)cvt_relu_e4m3x2(v1.x, v1.y) << 16);
+              }
+            }
+            tmem_st8(taddr + kAcol + 8 * part, w);
+            if constexpr (SPLIT) tmem_st8(taddr + kAlo + 8 * part, wl);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          named_bar_arrive(bar_a(q), kTile + 32);
+          return;
+        } else if constexpr (TA) {
           // ReLU -> FP16 pairs (split: hi and lo pairs) -> the slot's A columns
 #pragma unroll
           for (int part = 0; part < 2; ++part) {

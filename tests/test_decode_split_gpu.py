@@ -106,15 +106,16 @@ def test_split_empty_decode(nb, ctx):
         assert y.shape == (0, 9)
 
 
-@pytest.mark.parametrize("form", ["fp16", "fp16s", "fp32tc"])
+@pytest.mark.parametrize("form", ["fp16", "fp16s", "fp32tc", "fp8", "fp8s"])
 def test_tmem_and_shared_memory_operands_agree(nb, ctx, form):
-    """The FP16 tensor-core forms keep their MMA A operands in tensor memory
+    """The tensor-core forms keep their MMA A operands in tensor memory
     (default) or in shared memory (NBTC_TC_TMEM_A=0): the same products in the
     same order, so bit-identical outputs -- on a ragged grid (1024 x 200 plus a
     partial last tile) and a uv list."""
     dims = [12, 64, 64, 9] if form == "fp32tc" else [12, 64, 64, 64, 9]
     wl = synth.small_decode_workload(1024, dims, seed=440)
-    code = {"fp16": nb.FP16, "fp16s": nb.FP16_SPLIT, "fp32tc": nb.FP32_TC}[form]
+    code = {"fp16": nb.FP16, "fp16s": nb.FP16_SPLIT, "fp32tc": nb.FP32_TC, "fp8": nb.FP8_E4M3,
+            "fp8s": nb.FP8_E4M3_SPLIT}[form]
     os.environ["NBTC_TC_TMEM_A"] = "0"
     try:
         c2 = nb.Context(0)
@@ -125,8 +126,9 @@ def test_tmem_and_shared_memory_operands_agree(nb, ctx, form):
     for c in (ctx, c2):
         c.sync()
     outs = []
+    absmax = nb.fp8_calibrate(ctx, mat, 1024, 200, 16) if form.startswith("fp8") else None
     for c in (ctx, c2):
-        packed = nb.pack_mlp(c, mat, code)
+        packed = nb.pack_mlp(c, mat, code, act_absmax=absmax)
         outs.append((nb.decode(c, mat, code, packed, grid=(1024, 200)), nb.decode(c, mat, code, packed, uv=uv)))
         c.sync()
     iv = torch.int32 if form == "fp32tc" else torch.int16
