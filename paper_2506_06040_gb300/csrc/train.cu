@@ -263,6 +263,41 @@ __device__ __forceinline__ void sample_target(const TrainDev& a, float u, float 
   }
 }
 
+// The same taps and arithmetic as sample_target with every load issued before
+// the first blend (more registers; for k_gather, whose occupancy allows it).
+template <bool TV>
+__device__ __forceinline__ void sample_target_ilp(const TrainDev& a, float u, float v, float* out, int stride) {
+  Taps T = clamp_taps(u, v, a.tw, a.th, 0.f);
+  check_taps(T, (int64_t)a.tw * a.th, a);
+  const size_t ts = (size_t)a.ts;
+  const int C = a.C;
+  if constexpr (TV) {
+    // unrolled, loads first: every tap's loads are in flight at once
+    float4 v[kCMax / 4][4];
+#pragma unroll
+    for (int q = 0; q < kCMax / 4; ++q)
+      if (4 * q < C) {
+        v[q][0] = __ldg(reinterpret_cast<const float4*>(a.target + T.i00 * ts) + q);
+        v[q][1] = __ldg(reinterpret_cast<const float4*>(a.target + T.i10 * ts) + q);
+        v[q][2] = __ldg(reinterpret_cast<const float4*>(a.target + T.i01 * ts) + q);
+        v[q][3] = __ldg(reinterpret_cast<const float4*>(a.target + T.i11 * ts) + q);
+      }
+#pragma unroll
+    for (int q = 0; q < kCMax / 4; ++q) {
+      if (4 * q >= C) break;
+      const float4 v00 = v[q][0], v10 = v[q][1], v01 = v[q][2], v11 = v[q][3];
+      out[(4 * q) * stride] = T.w00 * v00.x + T.w10 * v10.x + T.w01 * v01.x + T.w11 * v11.x;
+      if (4 * q + 1 < C) out[(4 * q + 1) * stride] = T.w00 * v00.y + T.w10 * v10.y + T.w01 * v01.y + T.w11 * v11.y;
+      if (4 * q + 2 < C) out[(4 * q + 2) * stride] = T.w00 * v00.z + T.w10 * v10.z + T.w01 * v01.z + T.w11 * v11.z;
+      if (4 * q + 3 < C) out[(4 * q + 3) * stride] = T.w00 * v00.w + T.w10 * v10.w + T.w01 * v01.w + T.w11 * v11.w;
+    }
+  } else {
+    for (int c = 0; c < C; ++c)
+      out[c * stride] = T.w00 * __ldg(a.target + T.i00 * ts + c) + T.w10 * __ldg(a.target + T.i10 * ts + c) +
+                        T.w01 * __ldg(a.target + T.i01 * ts + c) + T.w11 * __ldg(a.target + T.i11 * ts + c);
+  }
+}
+
 // Floats per pre-gathered sample: 12 features (+ the target's C channels padded
 // to a multiple of 4 when the mode reads a target).
 __host__ __device__ inline int gathered_floats(int C, bool target) { return kIn + (target ? 4 * ((C + 3) / 4) : 0); }
@@ -286,7 +321,7 @@ __global__ void __launch_bounds__(256) k_gather(TrainDev a, float* __restrict__ 
       float tv[kCMax];
 #pragma unroll
       for (int c = 0; c < kCMax; ++c) tv[c] = 0.f;
-      sample_target<TV>(a, uv.x, uv.y, tv, 1);
+      sample_target_ilp<TV>(a, uv.x, uv.y, tv, 1);
 #pragma unroll
       for (int q = 0; q < kCMax / 4; ++q)
         if (4 * q < a.C) r[3 + q] = make_float4(tv[4 * q], tv[4 * q + 1], tv[4 * q + 2], tv[4 * q + 3]);
