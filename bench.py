@@ -297,13 +297,22 @@ TRAIN_MMA_FLOP_PER_SAMPLE = (2 * 128 * 64 * 16 * (4 + 13 + 3 + 12) + 2 * 128 * 1
                              2 * 64 * 16 * 16 * (24 + 16 + 24) + 2 * 64 * 64 * 16 * 24) // 128
 
 
+def _decode_wl(k: int, side: int):
+    """Decode workload k at its own side (4096), or a reduced side with the same
+    latent-to-output ratios (1/4 .. 1/32) and network, for profiling captures."""
+    if side == 4096:
+        return synth.decode_workload(k)
+    dims = {1: [12, 64, 64, 9], 2: [12, 64, 64, 64, 9]}[k]
+    return synth.small_decode_workload(side, dims, seed=1000 + k)
+
+
 def run_forms(args, nb, ctx, stream, flush, peaks, sm_count, ffma, form_ref) -> dict:
     """Precision forms on the 4096^2, 12-64-64-64-9 workload: FP32 SIMT, FP16 and
     FP8 E4M3 on tcgen05, single-rounding and split operands.  Error = per-channel
     max |form - FP64 oracle| over 1,048,576 texels (every 16th row), against the
     bound of the form's precision (FP16 2e-3, FP8 2e-2)."""
     import torch
-    wl = synth.decode_workload(2)
+    wl = _decode_wl(2, args.form_side)
     mat = nb.Material.from_synth(wl.material)
     W = H = args.form_side
     n = W * H
@@ -612,7 +621,7 @@ def run_ours(args, form_ref=None) -> dict | None:
     ctx = nb.Context(local)
     stream = torch.cuda.current_stream()
 
-    wl = synth.decode_workload(1)
+    wl = _decode_wl(1, args.side)
     mat = nb.Material.from_synth(wl.material)
     W = H = args.side
     n = W * H
@@ -781,9 +790,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--parts", default="main,forms,dsweep,train,batch",
                     help="comma list: main (always), forms, dsweep, train, batch")
-    ap.add_argument("--form-side", type=int, default=4096, help="output side of the precision-form workload")
+    ap.add_argument("--form-side", type=int, default=4096, help="output side of the precision-form workload "
+                    "(4096 = the benchmark workload; smaller sides keep its latent ratios, for profiling captures)")
     ap.add_argument("--side", type=int, default=4096, help="output side (4096 = the benchmark workload; "
-                    "smaller sides are for profiling captures)")
+                    "smaller sides keep its latent ratios, for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.parts = set(args.parts.split(","))
