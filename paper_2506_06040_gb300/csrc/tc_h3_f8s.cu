@@ -4,8 +4,8 @@
 namespace nbtc {
 
 nbtc_status launch_tc_h3_f8s(const TcArgs& p, int W, int slots, int grid, cudaStream_t s) {
-  if (p.tmem_a && W == 4 && slots == 1)  // A operands in TMEM
-    return launch_tc_w<3, kF8Split, 4, kModeSingle, 1, true>(p, grid, s);
+  if (p.tmem_a && W == 5 && slots == 1)  // A operands in TMEM: 5 warpgroups x 1 slot
+    return launch_tc_w<3, kF8Split, 5, kModeSingle, 1, true>(p, grid, s);
   if (slots != 2) return fail(NBTC_ERR_UNSUPPORTED, "this form runs two tile slots per warpgroup");
   return W == 3 ? launch_tc_w<3, kF8Split, 3, kModeSingle, 2>(p, grid, s) : launch_tc_w<3, kF8Split, 4, kModeSingle, 2>(p, grid, s);
 }

@@ -129,20 +129,20 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   constexpr bool OUT32 = FORM == kF32Split;                      // FP32 output
   constexpr int kSlots = NSL;
   constexpr int NS = W * kSlots;
-  // TMEM per slot: the accumulator (64 columns); with TA a 128-column slot
-  // holds the accumulator, then the slot's A operand: 64 FP16 = 32 columns
-  // (split forms: the hi tile, then the lo tile)
-  constexpr uint32_t kSlotCols = TA ? 2 * kHid : kHid;
-  constexpr uint32_t kAcol = kHid;                  // TA: A (hi) columns within a slot
-  // A of a hidden layer: 64 FP16 (32 columns) or 64 E4M3 (16 columns) per part
-  constexpr uint32_t kAlo = kHid + (FP8 ? kHid / 4 : kHid / 2);  // TA, split forms: lo columns
-  // TA, FP16: the bias products' A (ones) as an 8-column TMEM tile in the last
-  // slot's spare columns; the split forms read the shared-memory ones tile
+  // TMEM columns: the slots' FP32 accumulators first (64 columns each, on
+  // 64-column boundaries); with TA then every slot's A operand -- one part of a
+  // hidden layer's 64 activations is 32 columns of FP16 pairs or 16 of E4M3
+  // quads; split forms hold the hi part, then the lo part -- and, for the plain
+  // FP16 form, an 8-column tile of ones (the bias products' A; the split forms
+  // read the shared-memory ones tile)
+  constexpr uint32_t kApart = FP8 ? kHid / 4 : kHid / 2;
+  constexpr uint32_t kAcols = TA ? (SPLIT ? 2 : 1) * kApart : 0;
   constexpr bool kOnesT = TA && FORM == kF16;
-  constexpr uint32_t kOnesCol = (NS - 1) * kSlotCols + kAlo;
-  constexpr uint32_t kUsedCols = NS * kSlotCols;
+  constexpr uint32_t kOnesCol = NS * (kHid + kAcols);
+  constexpr uint32_t kUsedCols = NS * (kHid + kAcols) + (kOnesT ? 8 : 0);
   constexpr uint32_t kTmemCols = kUsedCols <= 256 ? 256 : 512;
   static_assert(kUsedCols <= 512, "TMEM holds at most 512 columns");
+  auto a_col = [](int q) { return (uint32_t)(NS * kHid) + (uint32_t)q * kAcols; };  // TA: slot q's A (hi)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const TcSmem S = tc_smem(L, W, NSL, TA);
@@ -290,12 +290,12 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
             named_bar_sync(bar_a(q), kTile + 32);
             if (lane == 0) {
               tc_fence_after();
-              const uint32_t d = tmem_base + (uint32_t)q * kSlotCols;
+              const uint32_t d = tmem_base + (uint32_t)q * kHid;
               const uint32_t slot = sbase + S.slots + q * S.slot;
               if constexpr (TA) {
                 // A from TMEM (8 columns per product: K = 16 FP16 or 32 E4M3),
                 // B from shared memory; the FP16 bias product's A is the ones tile
-                const uint32_t ah = d + kAcol, al = d + kAlo;
+                const uint32_t ah = tmem_base + a_col(q), al = ah + kApart;
                 if constexpr (FP8) {
                   if (l == 0) {
                     if constexpr (SPLIT) {
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
                   }
                 } else if (l == 0) {
                   if constexpr (F16S) {
-                    // A0: hi [x 1 000] in 8 columns at kAcol, lo [x 1 000] at kAlo
+                    // A0: hi [x 1 000] in the 8 columns at ah, lo [x 1 000] at al
                     mma_f16_ts(d, ah, dsc(hi_w1, lo_w1), ID_HID, 0);       // hi x . hi W + hi b
                     mma_f16_ts(d, al, dsc(hi_w1, lo_w1 + 16), ID_HID, 1);  // lo x . hi W + lo b
                     mma_f16_ts(d, ah, dsc(hi_w1, lo_w1 + 32), ID_HID, 1);  // hi x . lo W
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
             trilinear_features(work.m, uv.x, uv.y, __ldg(p.flod + pq), f);
         }
         if constexpr (TA) {
-          const uint32_t ta = tmem_base + (uint32_t)q * kSlotCols + lane_off;
+          const uint32_t ta = tmem_base + a_col(q) + lane_off;  // the slot's A (hi) columns
           if constexpr (FP8) {
             // A0 row of 32 E4M3: [x(12) 0 x 20], split: [hi x(12) 0000 | lo x(12) 0000]
             const float is = alpha[NHID + 1];  // 1 / input scale
@@ -472,20 +472,20 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
                        ((uint32_t)cvt_e4m3x2(f[4 * i + 2] * is, f[4 * i + 3] * is) << 16);
               }
             }
-            tmem_st8(ta + kAcol, w);
+            tmem_st8(ta, w);
           } else if constexpr (F16S) {
             uint32_t h[8], r[8];
 #pragma unroll
             for (int i = 0; i < 6; ++i) split_f16x2(f[2 * i], f[2 * i + 1], h[i], r[i]);
             h[6] = r[6] = 0x3C00u;  // k = 12: 1.0 for hi(b) / lo(b)
             h[7] = r[7] = 0u;
-            tmem_st8(ta + kAcol, h);
-            tmem_st8(ta + kAlo, r);
+            tmem_st8(ta, h);
+            tmem_st8(ta + kApart, r);
           } else {
             const uint32_t h[8] = {cvt_f16x2(f[0], f[1]), cvt_f16x2(f[2], f[3]),  cvt_f16x2(f[4], f[5]),
                                    cvt_f16x2(f[6], f[7]), cvt_f16x2(f[8], f[9]),  cvt_f16x2(f[10], f[11]),
                                    0x3C00u /* k = 12: 1.0 for the bias */, 0u};
-            tmem_st8(ta + kAcol, h);
+            tmem_st8(ta, h);
           }
           tmem_wait_st();
           tc_fence_before();
@@ -538,7 +538,8 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       // narrow -> Ah, then A-ready
       auto hidden_epilogue = [&](int s, int l) {
         const int q = wg * kSlots + s;
-        const uint32_t taddr = tmem_base + (uint32_t)q * kSlotCols + lane_off;
+        const uint32_t taddr = tmem_base + (uint32_t)q * kHid + lane_off;
+        const uint32_t aaddr = tmem_base + a_col(q) + lane_off;  // TA: the slot's A (hi) columns
         if constexpr (TA && FP8) {
           // scale and bias (packed FP32 FMAs), ReLU -> E4M3 quads (split: hi and
           // lo quads) -> the slot's A columns (8 per 32 activations)
@@ -566,8 +567,8 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
                 w[c] = (uint32_t)cvt_relu_e4m3x2(v0.x, v0.y) | ((uint32_t)cvt_relu_e4m3x2(v1.x, v1.y) << 16);
               }
             }
-            tmem_st8(taddr + kAcol + 8 * part, w);
-            if constexpr (SPLIT) tmem_st8(taddr + kAlo + 8 * part, wl);
+            tmem_st8(aaddr + 8 * part, w);
+            if constexpr (SPLIT) tmem_st8(aaddr + kApart + 8 * part, wl);
           }
           tmem_wait_st();
           tc_fence_before();
@@ -585,13 +586,13 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
 #pragma unroll
               for (int j = 0; j < 16; ++j)
                 split_relu_f16x2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]), h[j], lw[j]);
-              tmem_st16(taddr + kAlo + 16 * part, lw);
+              tmem_st16(aaddr + kApart + 16 * part, lw);
             } else {
 #pragma unroll
               for (int j = 0; j < 16; ++j)
                 h[j] = cvt_relu_f16x2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
             }
-            tmem_st16(taddr + kAcol + 16 * part, h);
+            tmem_st16(aaddr + 16 * part, h);
           }
           tmem_wait_st();
           tc_fence_before();
@@ -672,7 +673,7 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       // output epilogue of slot s, tile T: accumulator -> FP16 -> global
       auto output_epilogue = [&](int s, int64_t T) {
         const int q = wg * kSlots + s;
-        const uint32_t taddr = tmem_base + (uint32_t)q * kSlotCols + lane_off;
+        const uint32_t taddr = tmem_base + (uint32_t)q * kHid + lane_off;
         uint32_t r[16];
         tmem_ld16_wait(taddr, r);
         tc_fence_before();
