@@ -288,6 +288,9 @@ __global__ void __launch_bounds__(ttc::kWG * 160, 1) k_train_tc(TrainDev a) {
     for (int64_t tile = (int64_t)blockIdx.x * kWG + g; tile < tiles; tile += stride) {
       const int64_t sid = tile * 128 + t;
       const bool valid = sid < a.batch;
+      // the sample's uv for the latent scatter at the end of the tile, loaded now
+      // so its latency hides behind the tile's six phases
+      const float2 uv = valid ? __ldg(reinterpret_cast<const float2*>(a.uv) + sid) : make_float2(0.f, 0.f);
       // ---- 1: X (12 features, column 12 = 1 in the hi tile) and the target
       float tv[kCMax];
       {
@@ -306,6 +309,13 @@ __global__ void __launch_bounds__(ttc::kWG * 160, 1) k_train_tc(TrainDev a) {
             const float4 v = valid ? __ldg(rec + 3 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
             tv[4 * q] = v.x; tv[4 * q + 1] = v.y; tv[4 * q + 2] = v.z; tv[4 * q + 3] = v.w;
           }
+        // the next tile's record into L2 (its loads then wait on L2, not DRAM)
+        const int64_t nsid = (tile + stride) * 128 + t;
+        if (nsid < a.batch) {
+          const float* nrec = a.xt + nsid * a.rs;
+          sm100::prefetch_l2(nrec);
+          sm100::prefetch_l2(nrec + a.rs - 1);
+        }
         uint32_t h[8], l[8];
 #pragma unroll
         for (int i = 0; i < 6; ++i) split_f16x2(f[2 * i], f[2 * i + 1], h[i], l[i]);
@@ -382,7 +392,6 @@ __global__ void __launch_bounds__(ttc::kWG * 160, 1) k_train_tc(TrainDev a) {
         first_tile = false;
         tc_fence_before();
         if (valid) {
-          const float2 uv = __ldg(reinterpret_cast<const float2*>(a.uv) + sid);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             Taps Tp = clamp_taps(uv.x, uv.y, a.lw[k], a.lh[k], a.shift[k]);
