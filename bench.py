@@ -355,7 +355,7 @@ def run_forms(args, nb, ctx, stream, flush, peaks, sm_count, ffma, form_ref) -> 
                       "speedup_vs_fp32": ms / ms_tc,
                       "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
                                    "frac": ach / bf16, "executed_mma_tflops": exe, "executed_frac": exe / bf16,
-                                   "traffic": _profiled_traffic("k_decode_tc_fp32tc_4096sq"),
+                                   "traffic": None,  # profiled on the 12-64-64-9 workload (fp32_tc)
                                    "peak_source": "measured bf16 dense burst"}}
     absmax = nb.fp8_calibrate(ctx, mat, W, H, 16, stream=stream)
     packed = {"fp16_tc": nb.pack_mlp(ctx, mat, nb.FP16, stream=stream),
@@ -409,6 +409,7 @@ def run_fp32_tc(args, nb, ctx, stream, flush, peaks, mat, simt_ms, form_ref) -> 
         err = (out.view(4096, 4096, 9)[rows].reshape(-1, 9).double() - ref).abs().amax(dim=0).tolist()
     flop = FLOP_PER_TEXEL_C1 * n
     mma = 2 * (3 * 16 * 64 + (16 * 64 + 3 * 64 * 64) + 16 * 16 + 3 * 64 * 16)
+    algo = n * mat.n_out * 4 + sum(b.numel() * 8 for b in mat.blocks) + pk.numel() * pk.element_size()
     bf16 = peaks.get("bf16_tflops", 1900.0)
     ctx.sync(stream)
     return {"workload": WORKLOAD.replace("-fp32", "-fp32-tc"), "gtexel_s": n / ms / 1e6, "kernel_ms": ms,
@@ -417,7 +418,9 @@ def run_fp32_tc(args, nb, ctx, stream, flush, peaks, mat, simt_ms, form_ref) -> 
             "roofline": {"bound": "tensor", "achieved": flop / (ms * 1e-3) / 1e12, "peak": bf16, "unit": "TFLOP/s",
                          "frac": flop / (ms * 1e-3) / 1e12 / bf16, "executed_mma_flop_per_texel": mma,
                          "executed_frac": mma * n / (ms * 1e-3) / 1e12 / bf16,
-                         "peak_source": "measured bf16 dense burst"},
+                         "traffic": _profiled_traffic("k_decode_tc_fp32tc_4096sq"),
+                         "peak_source": "measured bf16 dense burst",
+                         "hbm": _hbm(algo, ms, peaks)},
             "note": "split FP16 operands (hi + lo, three products per layer) on tcgen05, FP32 accumulation and "
                     "output: the FP32 form's accuracy on tensor cores"}
 
