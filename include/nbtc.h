@@ -123,7 +123,7 @@ typedef struct nbtc_context nbtc_context;
  * device is not compute capability 10.3, NBTC_ERR_CUDA when CUDA fails.
  * Environment variables, read here, select kernel variants for measurement
  * (decode results are bit-identical either way): NBTC_TC_TMEM_A=0 keeps the
- * MMA A operands of the FP16 tensor-core forms (FP16, FP16_SPLIT, FP32_TC) in
+ * MMA A operands of the tensor-core forms (FP16, FP8_E4M3, both split forms, FP32_TC) in
  * shared memory instead of tensor memory; NBTC_TC_GROUPS=3 runs the
  * shared-memory-operand FP16 / FP8 decodes with 3 warpgroups per CTA instead of
  * 4; NBTC_FP32_GROUPS=1 runs the FP32 wide decode as one 512-thread group per

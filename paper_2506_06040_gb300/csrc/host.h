@@ -13,7 +13,7 @@ struct nbtc_context {
   int* status_dev = nullptr;       // device status word (first recorded fault)
   long long wait_budget = 0;       // spins per bounded device wait (0 = default, -1 = give up at once)
   int tc_groups = 4;               // warpgroups per CTA of the tensor-core decode (3 or 4)
-  int tc_tmem_a = 1;               // FP16 forms: A operands in TMEM (4 warpgroups x 1 slot; 0: shared memory)
+  int tc_tmem_a = 1;               // MMA A operands in TMEM (one slot per warpgroup; 0: shared memory)
   int fp32_groups = 2;             // independent thread groups per CTA of the FP32 wide decode (1 or 2)
   int check_plant = 0;             // checked build, tests only: offset added to gather indices
   int train_tc = 1;                // training steps with pre-gathered samples on tensor cores (0: SIMT)

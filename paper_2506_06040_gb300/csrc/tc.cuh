@@ -121,7 +121,7 @@ struct TcArgs {
   uint16_t* fout;          // frame: per-pixel output (nout FP16)
   int frame_w, tile_w, tile_h, tiles_x;
   int64_t frame_pixels;    // frame: pixel count (bounds of the checked build)
-  int tmem_a;              // FP16 form: 1 = A operands in TMEM (else shared memory)
+  int tmem_a;              // 1 = MMA A operands in TMEM (else shared memory)
 };
 
 // Per-CTA view of the chunk being decoded (in shared memory).

@@ -1,18 +1,22 @@
 // The tensor-core decode kernel (template; instantiated in tc_h*_*.cu).
 //
 // FP16 or FP8 E4M3 operands -- single or split into hi + lo pairs (three
-// products per layer) -- FP32 accumulation in TMEM, FP16 output: the GB300
-// counterpart of the paper's cooperative-vector MLP (Sec. 4, "Neural inference
-// in G-Buffer pass"); each layer of a 128-texel tile is one chain of
-// tcgen05.mma with M = 128 texels, N = layer width, weights resident in shared
-// memory.
+// products per layer) -- FP32 accumulation in TMEM, FP16 output (FP32 for the
+// FP32-accurate split form): the GB300 counterpart of the paper's
+// cooperative-vector MLP (Sec. 4, "Neural inference in G-Buffer pass"); each
+// layer of a 128-texel tile is one chain of tcgen05.mma with M = 128 texels,
+// N = layer width, weights resident in shared memory.
 //
 // Persistent, warp-specialised CTA (one per SM): W warpgroups of 128 threads
 // (one thread per tile row) compute features and run the epilogues, and
 // W warps (one per warpgroup) issue the MMAs.  Each warpgroup owns NSL tile
-// slots (TMEM columns + A buffers) and, with two, alternates between them, so
-// one slot's SIMT work overlaps the other slot's MMAs.  The CTA walks "chunks" -- runs of tiles of
-// one material -- and reloads the packed MLP only when the material changes.
+// slots.  With TA (the default) a slot is TMEM only -- its accumulator and the
+// next layer's A operand, which the epilogue writes back with tcgen05.st and
+// the MMAs read from TMEM -- one slot per warpgroup.  Without TA the A operands
+// are shared-memory tiles and a warpgroup with two slots alternates between
+// them, so one slot's SIMT work overlaps the other slot's MMAs.  The CTA walks
+// "chunks" -- runs of tiles of one material -- and reloads the packed MLP only
+// when the material changes.
 #pragma once
 
 #include <cstring>
@@ -55,11 +59,11 @@ __device__ __forceinline__ int64_t frame_pixel(const TcArgs& p, const WorkChunk&
   return px;
 }
 
-// Shared-memory plan.  Per slot: A0 (128 x K operand of layer 1) and Ah
-// (128 x 64 operand of later layers; split forms: hi tile then lo tile), and
-// the feature stage's column buffer (inside Ah while no MMA reads it).  The
-// FP16 split form lays A0 over the hi tile (A0 is consumed before the first
-// hidden epilogue writes Ah) and the column buffer over the lo tile.
+// Shared-memory plan: the packed MLP image, the ones tile, the per-warp output
+// staging and the barriers; with shared-memory A operands (not TA) also, per
+// slot, A0 (128 x K operand of layer 1) and Ah (128 x 64 operand of later
+// layers; split forms: hi tile then lo tile) -- the FP16 split form lays A0
+// over the hi tile (A0 is consumed before the first hidden epilogue writes Ah).
 struct TcSmem {
   int image;       // packed MLP (rounded to 1 KB)
   int ones;        // 128 x 16 FP16 tile of ones in column 0 (split: columns 0 and 1)
@@ -67,7 +71,6 @@ struct TcSmem {
   int slot;        // bytes per slot
   int a0, ah;      // offsets inside a slot
   int ah_lo;       // split forms: lo tile of Ah, from ah
-  int colbuf;      // column buffer, inside a slot
   int stage;       // per-warp output staging
   int bars;        // D-ready[NS], weight barrier, MMA-warp drain[W] (room for 2 NS + 1)
   int tslot;       // TMEM address slot
@@ -85,13 +88,11 @@ __host__ __device__ inline TcSmem tc_smem(const TcLayout& L, int W, int NSL, boo
     s.a0 = 0;
     s.ah = 0;
     s.ah_lo = 16384;
-    s.colbuf = 16384;
     s.slot = ta ? 0 : 32768;  // A operands in TMEM: no slot buffers
   } else {
     s.a0 = 0;
     s.ah = 4096;
     s.ah_lo = 8192;   // FP8 split: 128 x 64 E4M3 hi, then lo
-    s.colbuf = 4096;
     s.slot = ta ? 0 : 4096 + 16384;  // A operands in TMEM: no slot buffers
   }
   s.stage = s.slots + NS * s.slot;
