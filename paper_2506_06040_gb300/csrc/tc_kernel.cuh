@@ -427,12 +427,11 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       const int64_t g_end = min(g_begin + per_wg, range_end);
       StripCache cache;
       strip_reset(cache);
+      uint32_t next_a0[16];  // TA: the next tile's A0, computed during the output layer's MMAs
 
       // features of tile T (chunk numbering) into slot s's A0, then A-ready
-      auto start_tile = [&](int s, int64_t T) {
-        const int q = wg * kSlots + s;
-        const uint32_t a0 = sbase + S.slots + q * S.slot + S.a0;
-        float f[12];
+      // the 12 features of this thread's texel (or frame pixel) of tile T
+      auto tile_features = [&](int64_t T, float (&f)[12]) {
         if (MODE == kModeSingle || grid_chunk) {
           if (footprint) {
             // tile number = column block x H + row; each warp decodes its own
@@ -454,44 +453,61 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
           else
             trilinear_features(work.m, uv.x, uv.y, __ldg(p.flod + pq), f);
         }
-        if constexpr (TA) {
-          const uint32_t ta = tmem_base + a_col(q) + lane_off;  // the slot's A (hi) columns
-          if constexpr (FP8) {
-            // A0 row of 32 E4M3: [x(12) 0 x 20], split: [hi x(12) 0000 | lo x(12) 0000]
-            const float is = alpha[NHID + 1];  // 1 / input scale
-            uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+      };
+      // TA: a tile's A0 row as it goes into TMEM (8 columns; split FP16: hi in
+      // av[0..7], lo in av[8..15]), and its store + A-ready
+      auto pack_a0 = [&](const float (&f)[12], uint32_t (&av)[16]) {
+        if constexpr (FP8) {
+          // A0 row of 32 E4M3: [x(12) 0 x 20], split: [hi x(12) 0000 | lo x(12) 0000]
+          const float is = alpha[NHID + 1];  // 1 / input scale
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-              if constexpr (SPLIT) {
-                uint16_t h0, r0, h1, r1;
-                split_e4m3x2(cvt_f16x2(f[4 * i] * is, f[4 * i + 1] * is), h0, r0);
-                split_e4m3x2(cvt_f16x2(f[4 * i + 2] * is, f[4 * i + 3] * is), h1, r1);
-                w[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                w[4 + i] = (uint32_t)r0 | ((uint32_t)r1 << 16);
-              } else {
-                w[i] = (uint32_t)cvt_e4m3x2(f[4 * i] * is, f[4 * i + 1] * is) |
-                       ((uint32_t)cvt_e4m3x2(f[4 * i + 2] * is, f[4 * i + 3] * is) << 16);
-              }
+          for (int i = 0; i < 8; ++i) av[i] = 0u;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            if constexpr (SPLIT) {
+              uint16_t h0, r0, h1, r1;
+              split_e4m3x2(cvt_f16x2(f[4 * i] * is, f[4 * i + 1] * is), h0, r0);
+              split_e4m3x2(cvt_f16x2(f[4 * i + 2] * is, f[4 * i + 3] * is), h1, r1);
+              av[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+              av[4 + i] = (uint32_t)r0 | ((uint32_t)r1 << 16);
+            } else {
+              av[i] = (uint32_t)cvt_e4m3x2(f[4 * i] * is, f[4 * i + 1] * is) |
+                      ((uint32_t)cvt_e4m3x2(f[4 * i + 2] * is, f[4 * i + 3] * is) << 16);
             }
-            tmem_st8(ta, w);
-          } else if constexpr (F16S) {
-            uint32_t h[8], r[8];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) split_f16x2(f[2 * i], f[2 * i + 1], h[i], r[i]);
-            h[6] = r[6] = 0x3C00u;  // k = 12: 1.0 for hi(b) / lo(b)
-            h[7] = r[7] = 0u;
-            tmem_st8(ta, h);
-            tmem_st8(ta + kApart, r);
-          } else {
-            const uint32_t h[8] = {cvt_f16x2(f[0], f[1]), cvt_f16x2(f[2], f[3]),  cvt_f16x2(f[4], f[5]),
-                                   cvt_f16x2(f[6], f[7]), cvt_f16x2(f[8], f[9]),  cvt_f16x2(f[10], f[11]),
-                                   0x3C00u /* k = 12: 1.0 for the bias */, 0u};
-            tmem_st8(ta, h);
           }
-          tmem_wait_st();
-          tc_fence_before();
-          __syncwarp();
-          named_bar_arrive(bar_a(q), kTile + 32);
+        } else if constexpr (F16S) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) split_f16x2(f[2 * i], f[2 * i + 1], av[i], av[8 + i]);
+          av[6] = av[14] = 0x3C00u;  // k = 12: 1.0 for hi(b) / lo(b)
+          av[7] = av[15] = 0u;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) av[i] = cvt_f16x2(f[2 * i], f[2 * i + 1]);
+          av[6] = 0x3C00u;  // k = 12: 1.0 for the bias
+          av[7] = 0u;
+        }
+      };
+      auto store_a0 = [&](int s, const uint32_t (&av)[16]) {
+        const int q = wg * kSlots + s;
+        const uint32_t ta = tmem_base + a_col(q) + lane_off;  // the slot's A (hi) columns
+        tmem_st8(ta, av);
+        if constexpr (F16S) tmem_st8(ta + kApart, av + 8);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        named_bar_arrive(bar_a(q), kTile + 32);
+      };
+
+      // features of tile T (chunk numbering) into slot s's A0, then A-ready
+      auto start_tile = [&](int s, int64_t T) {
+        const int q = wg * kSlots + s;
+        const uint32_t a0 = sbase + S.slots + q * S.slot + S.a0;
+        float f[12];
+        tile_features(T, f);
+        if constexpr (TA) {
+          uint32_t av[16];
+          pack_a0(f, av);
+          store_a0(s, av);
           return;
         } else if constexpr (FORM == kF16) {
           sts128(a0 + off_interleave(gt, 0), cvt_f16x2(f[0], f[1]), cvt_f16x2(f[2], f[3]), cvt_f16x2(f[4], f[5]),
@@ -672,12 +688,18 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
       };
 
       // output epilogue of slot s, tile T: accumulator -> FP16 -> global
-      auto output_epilogue = [&](int s, int64_t T) {
+      // (TA, store_next: once the accumulator row is in registers, the next
+      // tile's A0 goes into TMEM and its layer-1 MMA may start while this
+      // epilogue converts and stores)
+      auto output_epilogue = [&](int s, int64_t T, bool store_next) {
         const int q = wg * kSlots + s;
         const uint32_t taddr = tmem_base + (uint32_t)q * kHid + lane_off;
         uint32_t r[16];
         tmem_ld16_wait(taddr, r);
         tc_fence_before();
+        if constexpr (TA) {
+          if (store_next) store_a0(s, next_a0);
+        }
         const float alp = alpha[NHID];
         const float* b = bias + NHID * kHid;
         uint16_t hv[kMaxOut];
@@ -786,9 +808,21 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
             tc_fence_after();
             if (l < NHID) {
               hidden_epilogue(s, l);
+              if constexpr (TA) {
+                // the next tile's features while the output layer's MMAs run
+                // (stored into TMEM once those have read this tile's A)
+                if (l == NHID - 1 && base + s + kSlots < g_end) {
+                  float f[12];
+                  tile_features(base + s + kSlots, f);
+                  pack_a0(f, next_a0);
+                }
+              }
             } else {
-              output_epilogue(s, base + s);
-              if (base + s + kSlots < g_end) start_tile(s, base + s + kSlots);
+              const bool more = base + s + kSlots < g_end;
+              output_epilogue(s, base + s, TA && more);
+              if constexpr (!TA) {
+                if (more) start_tile(s, base + s + kSlots);
+              }
             }
           }
         }
