@@ -145,7 +145,9 @@ __global__ void __launch_bounds__(W * 128 + 32 * W, 1) k_decode_tc(TcArgs p) {
   static_assert(kUsedCols <= 512, "TMEM holds at most 512 columns");
   auto a_col = [](int q) { return (uint32_t)(NS * kHid) + (uint32_t)q * kAcols; };  // TA: slot q's A (hi)
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // 1024-byte aligned base, formed by pointer arithmetic on the shared array so
+  // accesses through it compile to shared-memory loads (not generic ones)
+  unsigned char* smem = smem_raw + ((1024u - (uint32_t)(reinterpret_cast<uintptr_t>(smem_raw) & 1023u)) & 1023u);
   const TcSmem S = tc_smem(L, W, NSL, TA);
   const uint32_t sbase = smem_u32(smem);
   const int tid = threadIdx.x;
